@@ -1,0 +1,281 @@
+/*
+ * lbm.h -- C ABI of the GB300 library for the compressible Navier-Stokes-Fourier
+ * lattice Boltzmann scheme of Bukreev, Kummerlaender and Krause ("Lattice
+ * Boltzmann Method for Compressible Navier-Stokes-Fourier Equations").
+ *
+ * One time step (lbm_step) updates every cell of a 3-D grid with
+ *   - the zeroth moments Q_k of 14 D3Q7 population sets, one per component of
+ *     Q = (rho, rho u, E, tau, q)                                     (Eq. 2, Sec. 2.2)
+ *   - the closure p = (gamma-1)(E - rho|u|^2/2), T = p/rho and Sutherland's law
+ *                                                                     (Sec. 2.1, Listing 1)
+ *   - the cell-local shock sensor: dilatation from the cell's own moments,
+ *     s = max(0, -div u)/c_s, chi, omega_h = omega - chi (omega - omega_min),
+ *     omega = 1/tau_base, tau_base = 1/2 + 4 f_mu (mu/rho) dt/dx^2  (Sec. 2.3, Eqs. 3-6)
+ *   - BGK collision toward the linear equilibrium feq_{k,i} = w_i (Q_k + c_i.Phi_k/c_s^2)
+ *     with the source projected on the weights                       (Sec. 2.2)
+ *   - streaming along the lattice characteristics, in place           (Sec. 1, Sec. 2.2)
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an lbm_status; no exception or abort crosses the ABI.
+ *     On failure lbm_last_error() returns a message for the calling thread.
+ *   - Fields are numbered k = 0 rho, 1-3 rho u, 4 E, 5-10 tau (xx yy zz xy xz yz),
+ *     11-13 q; directions i = 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z.
+ *   - Cell index = x + nx (y + ny z). Per-cell arrays are [field][z][y][x];
+ *     population arrays are [k][i][z][y][x] in canonical order: the pre-collision
+ *     populations of the current time step, independent of the in-place storage.
+ *   - "dst_on_device"/"src_on_device" = 1: the pointer is device memory on the
+ *     handle's device; 0: host memory (pageable or pinned). The caller owns every
+ *     buffer it passes in; the library owns the device memory it allocates.
+ *   - Work is issued on the handle's CUDA stream (borrowed from the caller, or the
+ *     legacy default stream when none is given). Calls that return data to the
+ *     host synchronise that stream; lbm_step does not.
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;  /* one domain; opaque */
+typedef struct lbm_batch lbm_batch;    /* many independent domains; opaque */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_E_INVAL = 1,      /* bad argument or parameter */
+  LBM_E_NOMEM = 2,      /* device or host allocation failed */
+  LBM_E_CUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  LBM_E_NONFINITE = 4,  /* a non-finite moment was detected; sticky until re-init */
+  LBM_E_STATE = 5,      /* call not valid in the current state (e.g. step before init) */
+  LBM_E_IO = 6          /* checkpoint file could not be read or written, or is corrupt */
+} lbm_status;
+
+/* Population storage. All arithmetic is FP32 in every mode.
+ * F32: f - w_i Q_ref,k stored as float (the reference-shifted form of Sec. 2.2).
+ * F16 / BF16: (f - w_i Q_ref,k) / s_k stored as IEEE half / bfloat16, rounded to
+ * nearest even; s_k is fixed per field at init (see lbm_info). */
+typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 } lbm_store;
+
+/* Element types of data exchanged with the caller. NATIVE = the stored bits
+ * (4 bytes for F32 storage, 2 bytes otherwise), in canonical order. */
+typedef enum { LBM_DT_F32 = 0, LBM_DT_F64 = 1, LBM_DT_NATIVE = 2 } lbm_dtype;
+
+/* Selector of lbm_moments. */
+typedef enum {
+  LBM_MOM_Q = 0,     /* the 14 zeroth moments Q_k */
+  LBM_MOM_PRIM = 1   /* rho, u_x, u_y, u_z, T, p */
+} lbm_moment_set;
+
+/* Parameters of one domain (Table 1 and Sec. 2.1-2.3 of the paper). */
+typedef struct {
+  int nx, ny, nz;        /* cells per axis, each >= 1; nx*ny*nz < 2^31 */
+  int bc_x;              /* 0: periodic in x; 1: x ends held at the initial state
+                            (ghost layers keep the initial populations of the boundary
+                            cells; only their inward populations enter). y, z periodic. */
+  double dx;             /* lattice spacing, > 0 */
+  double dt;             /* > 0: time step; <= 0: dt = cfl * dx / (2 lambda_ref), i.e. the
+                            acoustic Courant number taken against c_s = c/2 (Table 1) */
+  double cfl;            /* acoustic Courant number (Table 1) */
+  double lambda_ref;     /* largest signal speed |u| + a of the problem, > 0 if dt <= 0 */
+  double gamma;          /* adiabatic index, > 1 */
+  double mu, kappa;      /* viscosity and conductivity (reference values if Sutherland) */
+  double tau_R, tau_q;   /* relaxation times of tau and q (Eq. 2), > 0 */
+  double T_ref;          /* Sutherland reference temperature, > 0 */
+  int relax_in_dt;       /* 1: tau_R, tau_q are given in units of dt (Sec. 3.1) */
+  int sutherland;        /* 1: mu_T = mu (1 + T_S) t^{3/2} / (t + T_S), t = T/T_ref,
+                            T_S = 0.4042, kappa_T = kappa mu_T/mu (Listing 1); 0: constant */
+  int source_mode;       /* 0: w_i dt S_k (explicit); 1: w_i (exp(-dt/tau) - 1) Q_k */
+  double f_mu;           /* background dissipation factor of Eq. 6, >= 0 */
+  double C_sigma;        /* sensor slope (Eq. 4), >= 0 */
+  double J_min;          /* sensor threshold on s (Eq. 4), >= 0 */
+  double omega_min;      /* floor of the blended rate (Eq. 5), in (0, 2] */
+  int sensor_mode;       /* 0: div u = (div(rho u) - u.grad rho)/rho from the cell's
+                            non-equilibrium moments; 1: div(rho u)/rho only */
+  int collide;           /* 1: collide and stream; 0: stream only (tests) */
+  int store;             /* lbm_store */
+  int use_graphs;        /* 1: lbm_step replays captured CUDA graphs of whole step pairs */
+  void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
+  void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
+                            256-byte aligned, borrowed for the handle's lifetime; NULL:
+                            the library allocates it */
+} lbm_params;
+
+/* Read-only facts of a handle. */
+typedef struct {
+  double dt, c;             /* time step and lattice speed dx/dt */
+  double tau_R, tau_q;      /* relaxation times in use (after relax_in_dt) */
+  double rho_ref, E_ref;    /* reference shift Q_ref (other components 0) */
+  double scale[14];         /* per-field storage scale s_k (1 for F32/BF16) */
+  long long step;           /* steps taken since the last init */
+  long long ncell;
+  size_t population_bytes;  /* bytes of the population buffer */
+  int store;
+  int block_x;              /* threads per block of the step kernel */
+} lbm_info_t;
+
+/* Diagnostics (Sec. 3.2, Eq. 7). Sums and extrema in FP64 over all cells.
+ * Velocity gradients by second-order central differences (periodic; one-sided
+ * at held x ends); mu_local follows the domain's viscosity law. */
+typedef struct {
+  double step, time;
+  double sum_rho, sum_mx, sum_my, sum_mz, sum_E;  /* sum over cells of Q_k */
+  double ek_mean;       /* <rho |u|^2 / 2> */
+  double eps_s_raw;     /* <mu_local |curl u|^2>; eps_s of Eq. 7 = eps_s_raw / rho_ref */
+  double eps_d_raw;     /* 4/3 <mu_local (div u)^2>; eps_d = eps_d_raw / rho_ref */
+  double max_mach;      /* max |u| / sqrt(gamma T) */
+  double max_cfl;       /* max over cells and axes of (|u_a| + a) dt / dx */
+  double min_rho, min_T;
+  double nonfinite;     /* cells with a non-finite zeroth moment */
+} lbm_diag_t;
+
+/* Kernel configuration chosen by the autotuner. */
+typedef struct {
+  int block_x;          /* threads per block of the step kernel */
+  float ms_per_step;    /* measured time of one step with that configuration */
+  int candidates;       /* configurations timed */
+} lbm_tune_t;
+
+/* ---- lifecycle -------------------------------------------------------------- */
+
+/* Bytes of the population buffer for these parameters: 98 arrays (14 fields x 7
+ * directions) of nx*ny*nz elements of the storage type, each array starting on a
+ * 256-byte boundary. Returns 0 if the sizes are invalid. */
+size_t lbm_population_bytes(const lbm_params* p);
+
+/* Validates *p (LBM_E_INVAL with the reason), derives dt and the relaxation
+ * times, allocates the device state on the current CUDA device (LBM_E_NOMEM if it
+ * does not fit) and returns an uninitialised handle in *out. The state is one
+ * population buffer updated in place; nothing of size O(cells) is allocated
+ * besides it until lbm_diag is first called. */
+lbm_status lbm_create(const lbm_params* p, lbm_handle** out);
+
+/* Releases everything the handle allocated (not borrowed buffers or streams).
+ * Waits for the handle's pending work. NULL is accepted. */
+lbm_status lbm_destroy(lbm_handle* h);
+
+/* Message of the last failed call made by this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* Name of a status code. */
+const char* lbm_status_string(lbm_status s);
+
+lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out);
+
+/* ---- initial states (Sec. 3) --------------------------------------------------
+ * Each sets every cell's populations to the linear equilibrium of its state with
+ * zero stress and heat flux (tau = q = 0), resets the step counter and the
+ * non-finite flag, records the held-x ghost populations, and fixes the storage
+ * reference Q_ref and (F16) the per-field scales s_k = max|f - w Q_ref| / 1024. */
+
+/* Supersonic Taylor-Green vortex of Sec. 3.2 on a box of side nx*dx = 2 pi L:
+ * u = U0 sin x cos y cos z, v = -U0 cos x sin y cos z, w = 0,
+ * p = p0 + rho0 U0^2/16 (cos 2x + cos 2y)(cos 2z + 2), p0 = rho0 U0^2/(gamma M0^2),
+ * uniform T0 = p0/rho0, rho = p/T0. Node (x,y,z) of cell (i,j,l) = (i,j,l) dx.
+ * Q_ref = (rho0, 0, 0, 0, p0/(gamma-1)). */
+lbm_status lbm_init_tgv(lbm_handle* h, double U0, double M0, double rho0);
+
+/* Riemann problem along `axis` (0,1,2): cells with index < i_split take
+ * left = (rho, u_axis, p), the others right. Q_ref = right state. */
+lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double left[3],
+                            const double right[3]);
+
+/* Equilibrium from caller fields [5][cells] = rho, u_x, u_y, u_z, p in `dtype`
+ * (LBM_DT_F32 or LBM_DT_F64) on the host or the device. Q_ref = (mean rho, 0, 0, 0,
+ * mean of p/(gamma-1) + rho|u|^2/2). */
+lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype);
+
+/* ---- the hot path ------------------------------------------------------------ */
+
+/* Advances n >= 0 time steps: per step one fused kernel reads each cell's 98
+ * populations (AA pattern: own slots on even steps, the neighbours' slots on odd
+ * steps), computes moments, closure, sensor and collision in FP32 and writes the
+ * 98 post-collision populations back in place, so that streaming happens through
+ * the index maps. Asynchronous on the handle's stream. Returns LBM_E_STATE before
+ * an init, LBM_E_NONFINITE if an earlier synchronising call saw non-finite
+ * moments (no work is issued then). */
+lbm_status lbm_step(lbm_handle* h, int n);
+
+/* Waits for the handle's stream; then reports LBM_E_NONFINITE if any step since
+ * the last init produced a non-finite moment (the flag is sticky). */
+lbm_status lbm_synchronize(lbm_handle* h);
+
+/* ---- outputs ------------------------------------------------------------------- */
+
+/* Per-cell moments of the current (pre-collision) state: `which` = LBM_MOM_Q
+ * (14 fields) or LBM_MOM_PRIM (6 fields), as [field][z][y][x] in `dtype`
+ * (LBM_DT_F32 or LBM_DT_F64), into dst on the host or device. Decoded and summed
+ * in FP64. Synchronises when dst is on the host. */
+lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, int dtype);
+
+/* Sensor of the current state, [3][z][y][x]: theta = div u (physical units),
+ * chi (Eq. 4) and omega_h (Eq. 5), exactly as the next step computes them (FP32
+ * arithmetic), written in `dtype` (F32 or F64). */
+lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype);
+
+/* FP64 reductions of Eq. 7 and conservation sums into *out (host). Allocates
+ * O(cells) device scratch on first use (kept until destroy). Synchronises. Also
+ * latches LBM_E_NONFINITE for later lbm_step calls when a non-finite moment is
+ * found (returned by this call as well, after *out is filled). */
+lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out);
+
+/* Canonical populations [k][i][z][y][x] in `dtype`: F64/F32 = the physical f
+ * (decoded), NATIVE = the stored bits. */
+lbm_status lbm_populations_get(lbm_handle* h, void* dst, int dst_on_device, int dtype);
+
+/* Replaces the state with canonical populations in `dtype` (F64/F32 are encoded
+ * into the storage type; NATIVE is copied bit for bit). With held x ends the
+ * inward populations of the boundary cells stay those of the ghost layer. Marks
+ * the handle initialised; the step counter is kept. A handle never initialised
+ * gets Q_ref = 0 and s_k = 1. */
+lbm_status lbm_populations_set(lbm_handle* h, const void* src, int src_on_device, int dtype);
+
+/* ---- checkpoint ---------------------------------------------------------------- */
+
+/* Writes the parameters, step counter, storage reference and scales, ghost
+ * layers and the raw population buffer (canonical order) to `path` with a CRC-32;
+ * lbm_load restores them into a handle with the same sizes and storage
+ * (LBM_E_INVAL otherwise, LBM_E_IO on a bad file). Resuming is bit-identical. */
+lbm_status lbm_save(lbm_handle* h, const char* path);
+lbm_status lbm_load(lbm_handle* h, const char* path);
+
+/* ---- tuning ------------------------------------------------------------------- */
+
+/* Times the step kernel for each candidate block size (whole step pairs, CUDA
+ * events on the handle's stream) and keeps the fastest in the handle; returns it
+ * in *out if out != NULL. Each candidate runs on the live state, so the state
+ * advances by an even number of steps: call it before init, or re-init after. */
+lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
+
+/* ---- many independent domains (batched mode) -------------------------------------
+ * n periodic domains with their own sizes and parameters (F32 storage), stored in
+ * one buffer. lbm_batch_step advances all of them by one step per persistent launch
+ * (grid = resident blocks of the GPU, blocks take work tiles from a table ordered
+ * largest domain first), replayed from a CUDA graph; lbm_batch_step_sequential
+ * issues one plain launch per domain per step instead (same arithmetic, for
+ * comparison). Tile size and block size come from lbm_batch_autotune. */
+lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out);
+lbm_status lbm_batch_destroy(lbm_batch* b);
+/* Per-domain TGV parameters, arrays of n values (host). */
+lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0,
+                              const double* rho0);
+lbm_status lbm_batch_step(lbm_batch* b, int n);
+lbm_status lbm_batch_step_sequential(lbm_batch* b, int n);
+lbm_status lbm_batch_synchronize(lbm_batch* b);
+/* lbm_moments of one domain. */
+lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int dst_on_device,
+                             int dtype);
+/* Total cells of all domains; time step of one domain. */
+lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain, double* dt);
+/* Times tile sizes x block sizes of the persistent kernel and keeps the fastest;
+ * advances the state like lbm_autotune. out may be NULL. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells,
+                              int* block_threads, float* ms_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H_ */

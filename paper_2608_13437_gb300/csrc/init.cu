@@ -1,0 +1,152 @@
+// Initial states (Sec. 3): TGV, Riemann problem, caller fields. Each cell gets the
+// linear equilibrium of its state with tau = q = 0, computed in FP64 and stored as
+// the deviation from w_i Q_ref in the storage type.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+// Macroscopic initial state (rho, u, p) of the cell.
+__device__ void initial_state(const DomainConst& P, const InitSpec& sp, int x, int y, int z,
+                              long long cell, double& rho, double u[3], double& p) {
+  if (sp.kind == 0) {
+    // Supersonic TGV (Sec. 3.2), nodes at (x, y, z) dx.
+    const double X = x * sp.dx, Y = y * sp.dx, Z = z * sp.dx;
+    const double p0 = sp.rho0 * sp.U0 * sp.U0 / (sp.gamma * sp.M0 * sp.M0);
+    const double T0 = p0 / sp.rho0;
+    u[0] = sp.U0 * sin(X) * cos(Y) * cos(Z);
+    u[1] = -sp.U0 * cos(X) * sin(Y) * cos(Z);
+    u[2] = 0.0;
+    p = p0 + sp.rho0 * sp.U0 * sp.U0 / 16.0 * (cos(2.0 * X) + cos(2.0 * Y)) * (cos(2.0 * Z) + 2.0);
+    rho = p / T0;
+  } else if (sp.kind == 1) {
+    const int idx = sp.axis == 0 ? x : (sp.axis == 1 ? y : z);
+    const double* s = idx < sp.split ? sp.left : sp.right;
+    rho = s[0];
+    u[0] = u[1] = u[2] = 0.0;
+    u[sp.axis] = s[1];
+    p = s[2];
+  } else {
+    const long long n = P.ncell;
+    if (sp.fields_f64) {
+      const double* f = static_cast<const double*>(sp.fields);
+      rho = f[cell]; u[0] = f[n + cell]; u[1] = f[2 * n + cell]; u[2] = f[3 * n + cell]; p = f[4 * n + cell];
+    } else {
+      const float* f = static_cast<const float*>(sp.fields);
+      rho = f[cell]; u[0] = f[n + cell]; u[1] = f[2 * n + cell]; u[2] = f[3 * n + cell]; p = f[4 * n + cell];
+    }
+  }
+}
+
+// Deviations d_{k,i} = feq_{k,i}(Q) - w_i Q_ref,k of the equilibrium with tau = q = 0.
+__device__ void equilibrium_dev(const DomainConst& P, const InitSpec& sp, double rho,
+                                const double u[3], double p, double dev[kF][kQ]) {
+  double Q[kF];
+  for (int k = 0; k < kF; ++k) Q[k] = 0.0;
+  Q[0] = rho;
+  for (int a = 0; a < 3; ++a) Q[1 + a] = rho * u[a];
+  Q[4] = p / (sp.gamma - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  Prim<double> s;
+  closure<double>(Q, sp.gamma - 1.0, sp.mu, sp.mu / sp.tau_R, sp.kappa / sp.tau_q, sp.inv_T_ref,
+                  sp.sutherland, s);
+  const double hic = 0.5 / sp.c;
+  for (int k = 0; k < kF; ++k) {
+    double fx, fy, fz;
+    field_flux<double>(k, s, fx, fy, fz);
+    const double qr = (k == 0) ? (double)P.rho_ref : (k == 4 ? (double)P.E_ref : 0.0);
+    const double D = Q[k] - qr;
+    dev[k][0] = 0.25 * D;
+    dev[k][1] = 0.125 * D + hic * fx;
+    dev[k][2] = 0.125 * D - hic * fx;
+    dev[k][3] = 0.125 * D + hic * fy;
+    dev[k][4] = 0.125 * D - hic * fy;
+    dev[k][5] = 0.125 * D + hic * fz;
+    dev[k][6] = 0.125 * D - hic * fz;
+  }
+}
+
+template <typename S>
+__global__ void k_init(const DomainConst P, const InitSpec sp, int mode, S* __restrict__ pop,
+                       float* __restrict__ ghost, unsigned* __restrict__ maxbits) {
+  const long long n = P.ncell;
+  const long long planes = (long long)P.ny * P.nz;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(cell % P.nx);
+    const long long yz = cell / P.nx;
+    const int y = (int)(yz % P.ny), z = (int)(yz / P.ny);
+    double rho, u[3], p;
+    initial_state(P, sp, x, y, z, cell, rho, u, p);
+    double dev[kF][kQ];
+    equilibrium_dev(P, sp, rho, u, p, dev);
+    if (mode == 0) {
+      for (int k = 0; k < kF; ++k) {
+        float m = 0.0f;
+        for (int i = 0; i < kQ; ++i) m = fmaxf(m, (float)fabs(dev[k][i]));
+        atomicMax(&maxbits[k], __float_as_uint(m));  // order of non-negative floats = order of bits
+      }
+      continue;
+    }
+    for (int k = 0; k < kF; ++k)
+      for (int i = 0; i < kQ; ++i)
+        pop[(long long)(k * kQ + i) * P.stride + cell] = Codec<S>::enc((float)dev[k][i], P.inv_scale[k]);
+    if (P.bc_x && ghost) {
+      const long long plane = yz;
+      if (x == 0)
+        for (int k = 0; k < kF; ++k) ghost[(0 * kF + k) * planes + plane] = (float)dev[k][1];
+      if (x == P.nx - 1)
+        for (int k = 0; k < kF; ++k) ghost[(1LL * kF + k) * planes + plane] = (float)dev[k][2];
+    }
+  }
+}
+
+__global__ void k_field_means(const DomainConst P, const InitSpec sp, double* sums) {
+  double s_rho = 0.0, s_E = 0.0;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    double rho, u[3], p;
+    initial_state(P, sp, 0, 0, 0, cell, rho, u, p);
+    s_rho += rho;
+    s_E += p / (sp.gamma - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s_rho += __shfl_down_sync(0xffffffffu, s_rho, o);
+    s_E += __shfl_down_sync(0xffffffffu, s_E, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], s_rho);
+    atomicAdd(&sums[1], s_E);
+  }
+}
+
+int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
+                        float* ghost, unsigned* maxbits, cudaStream_t s) {
+  const int block = 128;
+  const int grid = grid_for(P.ncell, block);
+  switch (store) {
+    case 0: k_init<float><<<grid, block, 0, s>>>(P, spec, mode, static_cast<float*>(pop), ghost, maxbits); break;
+    case 1: k_init<__half><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__half*>(pop), ghost, maxbits); break;
+    default: k_init<__nv_bfloat16><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__nv_bfloat16*>(pop), ghost, maxbits); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const int block = 256;
+  k_field_means<<<grid_for(P.ncell, block), block, 0, s>>>(P, spec, sums);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,190 @@
+// Outputs of the current state through the AA read map of its parity: per-cell
+// moments (FP64 sums), the sensor exactly as the next step computes it, and
+// canonical population arrays in and out.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ void decompose(const DomainConst& P, long long cell, int& x, int& y,
+                                          int& z) {
+  x = (int)(cell % P.nx);
+  const long long yz = cell / P.nx;
+  y = (int)(yz % P.ny);
+  z = (int)(yz / P.ny);
+}
+
+template <typename S>
+__device__ __forceinline__ double read_dev64(const DomainConst& P, const S* pop, const float* ghost,
+                                             const CellIndex& c, int parity, int k, int i) {
+  if (from_ghost(P, c, i)) return (double)ghost_value(P, ghost, c, k, i);
+  return Codec<S>::dec64(pop[read_pos(P, c, parity, k, i)], (double)P.scale[k]);
+}
+
+template <typename S>
+__global__ void k_moments(const DomainConst P, int parity, const S* __restrict__ pop,
+                          const float* __restrict__ ghost, int which, void* out, int out_f64,
+                          long long c0, long long cnt) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < cnt;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long cell = c0 + r;
+    int x, y, z;
+    decompose(P, cell, x, y, z);
+    const CellIndex c = make_index(P, x, y, z);
+    double Q[kF];
+    for (int k = 0; k < kF; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kQ; ++i) s += read_dev64(P, pop, ghost, c, parity, k, i);
+      Q[k] = s;
+    }
+    Q[0] += (double)P.rho_ref;
+    Q[4] += (double)P.E_ref;
+    double v[kF];
+    int nv = kF;
+    if (which == 1) {
+      Prim<double> s;
+      closure<double>(Q, P.gm1_64, 0.0, 0.0, 0.0, 1.0, 0, s);
+      v[0] = s.rho; v[1] = s.u[0]; v[2] = s.u[1]; v[3] = s.u[2]; v[4] = s.T; v[5] = s.p;
+      nv = 6;
+    } else {
+      for (int k = 0; k < kF; ++k) v[k] = Q[k];
+    }
+    for (int j = 0; j < nv; ++j) {
+      if (out_f64) static_cast<double*>(out)[(long long)j * cnt + r] = v[j];
+      else static_cast<float*>(out)[(long long)j * cnt + r] = (float)v[j];
+    }
+  }
+}
+
+template <typename S>
+__global__ void k_sensor(const DomainConst P, int parity, const S* __restrict__ pop,
+                         const float* __restrict__ ghost, void* out, int out_f64, long long c0,
+                         long long cnt) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < cnt;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long cell = c0 + r;
+    int x, y, z;
+    decompose(P, cell, x, y, z);
+    const CellIndex c = make_index(P, x, y, z);
+    float d[kF][kQ];
+    if (parity) {
+      if (P.bc_x) load_cell<1, true, S>(P, pop, ghost, c, d);
+      else load_cell<1, false, S>(P, pop, ghost, c, d);
+    } else {
+      if (P.bc_x) load_cell<0, true, S>(P, pop, ghost, c, d);
+      else load_cell<0, false, S>(P, pop, ghost, c, d);
+    }
+    SensorOut so;
+    collide_cell<true>(P, d, &so);
+    const double v[3] = {(double)so.theta_dt / (double)P.dt, (double)so.chi, (double)so.omega_h};
+    for (int j = 0; j < 3; ++j) {
+      if (out_f64) static_cast<double*>(out)[(long long)j * cnt + r] = v[j];
+      else static_cast<float*>(out)[(long long)j * cnt + r] = (float)v[j];
+    }
+  }
+}
+
+__device__ __forceinline__ double weight(int i) { return i == 0 ? 0.25 : 0.125; }
+
+__device__ __forceinline__ double ref_of(const DomainConst& P, int k) {
+  return k == 0 ? (double)P.rho_ref : (k == 4 ? (double)P.E_ref : 0.0);
+}
+
+template <typename S>
+__global__ void k_pop_get(const DomainConst P, int parity, const S* __restrict__ pop,
+                          const float* __restrict__ ghost, int k, int i, void* out, int dtype) {
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    decompose(P, cell, x, y, z);
+    const CellIndex c = make_index(P, x, y, z);
+    if (dtype == 2) {  // native bits; the ghost value is encoded like a stored one
+      S g = from_ghost(P, c, i) ? Codec<S>::enc(ghost_value(P, ghost, c, k, i), P.inv_scale[k])
+                                : pop[read_pos(P, c, parity, k, i)];
+      static_cast<S*>(out)[cell] = g;
+      continue;
+    }
+    const double f = weight(i) * ref_of(P, k) + read_dev64(P, pop, ghost, c, parity, k, i);
+    if (dtype == 1) static_cast<double*>(out)[cell] = f;
+    else static_cast<float*>(out)[cell] = (float)f;
+  }
+}
+
+template <typename S>
+__global__ void k_pop_set(const DomainConst P, int parity, S* __restrict__ pop, int k, int i,
+                          const void* in, int dtype) {
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    decompose(P, cell, x, y, z);
+    const CellIndex c = make_index(P, x, y, z);
+    if (from_ghost(P, c, i)) continue;  // held ends keep the ghost inflow
+    S g;
+    if (dtype == 2) {
+      g = static_cast<const S*>(in)[cell];
+    } else {
+      const double f = dtype == 1 ? static_cast<const double*>(in)[cell]
+                                  : (double)static_cast<const float*>(in)[cell];
+      g = Codec<S>::enc((float)(f - weight(i) * ref_of(P, k)), P.inv_scale[k]);
+    }
+    pop[read_pos(P, c, parity, k, i)] = g;
+  }
+}
+
+int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+
+cudaError_t launch_moments(const DomainConst& P, int store, int parity, const void* pop,
+                           const float* ghost, int which, void* out, int out_f64, long long c0,
+                           long long cnt, cudaStream_t s) {
+  const int block = 128, grid = grid_for(cnt, block);
+  switch (store) {
+    case 0: k_moments<float><<<grid, block, 0, s>>>(P, parity, (const float*)pop, ghost, which, out, out_f64, c0, cnt); break;
+    case 1: k_moments<__half><<<grid, block, 0, s>>>(P, parity, (const __half*)pop, ghost, which, out, out_f64, c0, cnt); break;
+    default: k_moments<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (const __nv_bfloat16*)pop, ghost, which, out, out_f64, c0, cnt); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensor(const DomainConst& P, int store, int parity, const void* pop,
+                          const float* ghost, void* out, int out_f64, long long c0, long long cnt,
+                          cudaStream_t s) {
+  const int block = 128, grid = grid_for(cnt, block);
+  switch (store) {
+    case 0: k_sensor<float><<<grid, block, 0, s>>>(P, parity, (const float*)pop, ghost, out, out_f64, c0, cnt); break;
+    case 1: k_sensor<__half><<<grid, block, 0, s>>>(P, parity, (const __half*)pop, ghost, out, out_f64, c0, cnt); break;
+    default: k_sensor<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (const __nv_bfloat16*)pop, ghost, out, out_f64, c0, cnt); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pop_get(const DomainConst& P, int store, int parity, const void* pop,
+                           const float* ghost, int k, int i, void* out, int dtype, cudaStream_t s) {
+  const int block = 256, grid = grid_for(P.ncell, block);
+  switch (store) {
+    case 0: k_pop_get<float><<<grid, block, 0, s>>>(P, parity, (const float*)pop, ghost, k, i, out, dtype); break;
+    case 1: k_pop_get<__half><<<grid, block, 0, s>>>(P, parity, (const __half*)pop, ghost, k, i, out, dtype); break;
+    default: k_pop_get<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (const __nv_bfloat16*)pop, ghost, k, i, out, dtype); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pop_set(const DomainConst& P, int store, int parity, void* pop, int k, int i,
+                           const void* in, int dtype, cudaStream_t s) {
+  const int block = 256, grid = grid_for(P.ncell, block);
+  switch (store) {
+    case 0: k_pop_set<float><<<grid, block, 0, s>>>(P, parity, (float*)pop, k, i, in, dtype); break;
+    case 1: k_pop_set<__half><<<grid, block, 0, s>>>(P, parity, (__half*)pop, k, i, in, dtype); break;
+    default: k_pop_set<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (__nv_bfloat16*)pop, k, i, in, dtype); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,58 @@
+// Host-side declarations shared by the translation units of liblbm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Fused step: one launch per time step, grid (ceil(nx/block_x), ny, nz).
+cudaError_t launch_step_f32(const DomainConst& P, int parity, void* pop, const float* ghost,
+                            unsigned* flag, int block_x, cudaStream_t s);
+cudaError_t launch_step_f16(const DomainConst& P, int parity, void* pop, const float* ghost,
+                            unsigned* flag, int block_x, cudaStream_t s);
+cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const float* ghost,
+                             unsigned* flag, int block_x, cudaStream_t s);
+
+// Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields.
+struct InitSpec {
+  int kind;
+  double U0, M0, rho0;                 // TGV
+  int axis, split;                     // Riemann
+  double left[3], right[3];
+  const void* fields;                  // [5][cell] rho, ux, uy, uz, p on the device
+  int fields_f64;
+  double gamma, mu, kappa, tau_R, tau_q, inv_T_ref, c, dx;
+  int sutherland;
+};
+// mode 0: per-field max |f - w Q_ref| into maxbits[14] (float bits); mode 1: write
+// the encoded populations (canonical slots) and the held-x ghost layers.
+cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
+                        float* ghost, unsigned* maxbits, cudaStream_t s);
+// Sums of rho and E = p/(gamma-1) + rho|u|^2/2 over caller fields into sums[2] (zeroed here).
+cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
+                               cudaStream_t s);
+
+// Outputs (io.cu); parity and held-x are runtime values here.
+// Cells [c0, c0 + cnt) into out[field][cnt].
+cudaError_t launch_moments(const DomainConst& P, int store, int parity, const void* pop,
+                           const float* ghost, int which, void* out, int out_f64, long long c0,
+                           long long cnt, cudaStream_t s);
+cudaError_t launch_sensor(const DomainConst& P, int store, int parity, const void* pop,
+                          const float* ghost, void* out, int out_f64, long long c0, long long cnt,
+                          cudaStream_t s);
+// One population array (k, i) in canonical order, decoded (dtype F32/F64) or native.
+cudaError_t launch_pop_get(const DomainConst& P, int store, int parity, const void* pop,
+                           const float* ghost, int k, int i, void* out, int dtype, cudaStream_t s);
+cudaError_t launch_pop_set(const DomainConst& P, int store, int parity, void* pop, int k, int i,
+                           const void* in, int dtype, cudaStream_t s);
+
+// Diagnostics (diag.cu).
+constexpr int kDiagA = 13;  // sums: rho mx my mz E ke nonfinite | max: mach cfl | min: rho T
+constexpr int kDiagBlocks = 1216;
+cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void* pop,
+                        const float* ghost, double* ufield, double* partials, double* out16,
+                        cudaStream_t s);
+
+}  // namespace lbm

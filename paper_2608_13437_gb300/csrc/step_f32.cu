@@ -1,0 +1,9 @@
+// Fused step kernels for float population storage.
+#include "step_impl.cuh"
+
+namespace lbm {
+cudaError_t launch_step_f32(const DomainConst& P, int parity, void* pop, const float* ghost,
+                          unsigned* flag, int block_x, cudaStream_t s) {
+  return launch_step_t<float>(P, parity, pop, ghost, flag, block_x, s);
+}
+}  // namespace lbm

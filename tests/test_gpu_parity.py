@@ -1,0 +1,312 @@
+"""GPU path against the FP64 oracle, through the C ABI.
+
+Bar: streaming bit-exact (every storage type, both AA parities); FP32 storage and
+arithmetic within a relative L2 of 1e-5 of the oracle on rho, u and T after 100
+smooth steps; Sod shock position within 1e-3.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from conftest import make_oracle
+from paper_2608_13437_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+NF, NQ = 14, 7
+E = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_13437_gb300 import build, lbm as L
+    build.build()
+    L.lib()
+    return L
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def prim_errors(gpu, ref):
+    """rel-L2 of rho, |u| (vector), T."""
+    return {"rho": rel_l2(gpu[0], ref[0]), "u": rel_l2(gpu[1:4], ref[1:4]), "T": rel_l2(gpu[4], ref[4])}
+
+
+# --------------------------------------------------------------------------- streaming
+@pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape,steps", [((5, 4, 3), 1), ((5, 4, 3), 2), ((37, 6, 5), 7),
+                                         ((1, 1, 1), 3), ((64, 3, 2), 10)])
+def test_streaming_bit_exact(lbm, oracle_mod, store, shape, steps):
+    """Collision off: the AA index maps must realise f_i(x) <- f_i(x - e_i) exactly,
+    for odd and even step counts, ragged sizes and a single cell. The expected
+    values come from the oracle's pull streaming of the same labels."""
+    nx, ny, nz = shape
+    p = inputs.tgv_params(8)
+    p.update(nx=nx, ny=ny, nz=nz, collide=0)
+    dom = lbm.Domain(p, store=store)
+    if store == "f32":
+        lab = inputs.random_labels((NF, NQ, nz, ny, nx), seed=3, dtype=np.float32)
+        ref_in = lab.astype(np.float64)
+    else:
+        # distinct finite 16-bit patterns (positive normal numbers of either format)
+        rng = np.random.default_rng(5)
+        lab = (0x0400 + rng.permutation(NF * NQ * nx * ny * nz) % 0x3800).astype(np.uint16)
+        lab = lab.reshape(NF, NQ, nz, ny, nx)
+        ref_in = lab.astype(np.float64)  # the oracle permutes bit patterns as numbers
+    dom.set_populations(lab, native=True)
+    dom.step(steps)
+    got = dom.populations("native")
+    q = dict(p)
+    o = make_oracle(q)
+    o.set_populations(ref_in)
+    o.step(steps)
+    ref = o.populations()
+    assert np.array_equal(got.astype(np.float64), ref)
+    # the same permutation written out with np.roll
+    exp = np.empty_like(lab)
+    for i in range(NQ):
+        exp[:, i] = np.roll(lab[:, i], shift=(steps * E[i, 2], steps * E[i, 1], steps * E[i, 0]),
+                            axis=(1, 2, 3))
+    assert np.array_equal(got, exp)
+    dom.close()
+
+
+# --------------------------------------------------------------------------- smooth parity
+def _tgv_pair(lbm, n, steps, store="f32", **over):
+    p = inputs.tgv_params(n)
+    p.update(over)
+    dom = lbm.Domain(p, store=store)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.step(steps)
+    dom.synchronize()
+    o = make_oracle(p)
+    o.init_tgv(1.0, 1.25, 1.0)
+    o.step(steps)
+    return dom, o
+
+
+@pytest.mark.parametrize("steps", [100, 101])
+def test_tgv_fp32_matches_fp64_oracle(lbm, oracle_mod, steps):
+    """Supersonic TGV 32^3 (M0 1.25, Re 1000): after 100 (even parity) and 101 (odd
+    parity) steps rho, u, T agree with the FP64 oracle within rel-L2 1e-5; the
+    sensor is active in part of the box."""
+    dom, o = _tgv_pair(lbm, 32, steps)
+    assert abs(dom.dt - o.dt) <= 1e-15 * o.dt
+    err = prim_errors(dom.primitives(), o.primitives())
+    assert max(err.values()) < 1e-5, err
+    _, chi, _ = o.sensor()
+    assert (chi > 0).mean() > 0.01
+    Qg, Qo = dom.moments(), o.moments()
+    # stress and heat flux: small fields, compared relative to their own norm
+    assert rel_l2(Qg[5:11], Qo[5:11]) < 1e-3
+    assert rel_l2(Qg[11:14], Qo[11:14]) < 1e-3
+    dom.close()
+
+
+def test_ragged_random_state_matches_oracle(lbm, oracle_mod):
+    """A ragged 20 x 12 x 9 box (x shorter than a warp, tails everywhere) from a seeded
+    random smooth state, sensor active, constant viscosity, 41 steps."""
+    nx, ny, nz = 20, 12, 9
+    p = inputs.tgv_params(16)
+    p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / 20, sutherland=0, f_mu=0.3, J_min=1e-3,
+             tau_R=0.05, tau_q=0.05)
+    s = inputs.random_smooth_state(nx, ny, nz, seed=17, amp=0.15)
+    dom = lbm.Domain(p)
+    dom.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"])
+    o = make_oracle(p)
+    o.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"])
+    dom.step(41)
+    o.step(41)
+    err = prim_errors(dom.primitives(), o.primitives())
+    assert max(err.values()) < 1e-5, err
+    _, chi, _ = o.sensor()
+    assert (chi > 0).any()
+    dom.close()
+
+
+def test_sensor_matches_oracle_on_same_state(lbm, oracle_mod):
+    """Sensor outputs (theta, chi, omega_h) of the GPU on a state taken from the
+    oracle after 5 TGV steps equal the oracle's up to FP32 rounding; chi may differ
+    only where s sits within rounding of J_min."""
+    p = inputs.tgv_params(32)
+    o = make_oracle(p)
+    o.init_tgv(1.0, 1.25, 1.0)
+    o.step(5)
+    f = o.populations()
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)  # sets the storage reference
+    dom.set_populations(f)
+    th_g, chi_g, om_g = dom.sensor()
+    th_o, chi_o, om_o = o.sensor()
+    scale = np.abs(th_o).max()
+    assert np.abs(th_g - th_o).max() < 1e-3 * scale
+    s_o = 2 * np.maximum(0, -th_o * o.dt)
+    near = np.abs(s_o - p["J_min"]) < 1e-4
+    assert np.allclose(chi_g[~near], chi_o[~near], rtol=1e-4, atol=1e-5)
+    assert np.allclose(om_g[~near], om_o[~near], rtol=1e-5)
+    dom.close()
+
+
+def test_sod_matches_oracle_and_exact(lbm, oracle_mod):
+    """Sod on 1024 x 4 x 4, x ends held, to t = 0.2: shock position within 1e-3 of
+    the oracle's and of the exact solution; density profile close to the oracle's."""
+    from oracle import riemann
+    n = 1024
+    p = inputs.sod_params(n)
+    dom = lbm.Domain(p)
+    dom.init_riemann(0, n // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    steps = inputs.sod_steps(dom.dt)
+    dom.step(steps)
+    dom.synchronize()
+    P = dom.primitives()
+    assert np.allclose(P[:, :, :, :], P[:, :1, :1, :], rtol=0, atol=1e-6)  # uniform in y, z
+    rho_g = P[0, 0, 0]
+    q = inputs.sod_params(n, ny=1, nz=1)
+    o = make_oracle(q)
+    o.init_riemann(0, n // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    assert inputs.sod_steps(o.dt) == steps
+    o.step(steps)
+    rho_o = o.primitives()[0, 0, 0]
+    x = (np.arange(n) + 0.5) / n
+    t = steps * dom.dt
+
+    def shock(rho):
+        st = riemann.solve_star(riemann.State(*inputs.SOD_LEFT), riemann.State(*inputs.SOD_RIGHT))
+        mid = 0.5 * (st.rho_R + inputs.SOD_RIGHT[0])
+        right = x[:-1] > 0.5 + st.u * t + 0.05
+        i = np.where(right & (rho[:-1] >= mid) & (rho[1:] < mid))[0][-1]
+        return x[i] + (rho[i] - mid) / (rho[i] - rho[i + 1]) / n
+
+    xs_exact = riemann.shock_position(riemann.State(*inputs.SOD_LEFT),
+                                      riemann.State(*inputs.SOD_RIGHT), t, 0.5)
+    assert abs(shock(rho_g) - shock(rho_o)) < 1e-3
+    assert abs(shock(rho_g) - xs_exact) < 1e-3
+    assert np.mean(np.abs(rho_g - rho_o)) < 1e-3
+    dom.close()
+
+
+# --------------------------------------------------------------------------- 16-bit storage
+@pytest.mark.parametrize("store,bound", [("f16", 2e-3), ("bf16", 2e-2)])
+def test_reduced_storage_error_vs_oracle(lbm, oracle_mod, store, bound):
+    """FP16 / BF16 shifted-deviation storage with FP32 collision: the error against
+    the FP64 oracle after 100 TGV steps at 32^3 is finite and below a stated bound."""
+    dom, o = _tgv_pair(lbm, 32, 100, store=store)
+    err = prim_errors(dom.primitives(), o.primitives())
+    assert all(np.isfinite(v) for v in err.values())
+    assert max(err.values()) < bound, err
+    print(store, err)
+    dom.close()
+
+
+# --------------------------------------------------------------------------- invariants
+def test_uniform_state_fixed_point_gpu(lbm):
+    p = inputs.tgv_params(8)
+    p.update(nx=12, ny=7, nz=5)
+    dom = lbm.Domain(p)
+    sh = (5, 7, 12)
+    dom.init_fields(np.full(sh, 1.1), np.full(sh, 0.3), np.full(sh, -0.2), np.full(sh, 0.1),
+                    np.full(sh, 0.9))
+    f0 = dom.populations()
+    dom.step(9)
+    f1 = dom.populations()
+    assert np.abs(f1 - f0).max() < 1e-6 * np.abs(f0).max()
+    dom.close()
+
+
+def test_conservation_gpu(lbm):
+    """Mass, momentum and energy totals after 200 FP32 steps stay at their initial
+    values to FP32 round-off (reported from the FP64 diagnostics)."""
+    p = inputs.tgv_params(32)
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    d0 = dom.diag()
+    dom.step(200)
+    d1 = dom.diag()
+    assert abs(d1["sum_rho"] / d0["sum_rho"] - 1) < 1e-6
+    assert abs(d1["sum_E"] / d0["sum_E"] - 1) < 1e-6
+    for c in ("sum_mx", "sum_my", "sum_mz"):
+        assert abs(d1[c] - d0[c]) < 1e-6 * d0["sum_rho"]
+    dom.close()
+
+
+def test_diag_matches_oracle(lbm, oracle_mod):
+    dom, o = _tgv_pair(lbm, 32, 40)
+    g, r = dom.diag(), o.diag()
+    for k in ("sum_rho", "sum_E", "ek_mean", "min_rho", "min_T", "max_mach", "max_cfl"):
+        assert g[k] == pytest.approx(r[k], rel=2e-6), k
+    for k in ("eps_s_raw", "eps_d_raw"):
+        assert g[k] == pytest.approx(r[k], rel=1e-4), k
+    assert g["nonfinite"] == 0 and g["step"] == 40
+    dom.close()
+
+
+def test_graphs_and_direct_launches_agree_bitwise(lbm):
+    p = inputs.tgv_params(32)
+    a = lbm.Domain(p, use_graphs=True)
+    b = lbm.Domain(p, use_graphs=False)
+    for d in (a, b):
+        d.init_tgv(1.0, 1.25, 1.0)
+        d.step(1)
+        d.step(70)
+    assert np.array_equal(a.populations("native"), b.populations("native"))
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_is_bit_identical(lbm):
+    p = inputs.tgv_params(16)
+    a = lbm.Domain(p)
+    a.init_tgv(1.0, 1.25, 1.0)
+    a.step(13)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ck.bin")
+        a.save(path)
+        a.step(10)
+        b = lbm.Domain(p)
+        b.load(path)
+        assert b.info()["step"] == 13
+        b.step(10)
+        assert np.array_equal(a.populations("native"), b.populations("native"))
+        with open(path, "r+b") as fh:  # corrupt one byte: the CRC must catch it
+            fh.seek(4000)
+            byte = fh.read(1)
+            fh.seek(4000)
+            fh.write(bytes([byte[0] ^ 0xFF]))
+        with pytest.raises(lbm.LbmError) as ei:
+            b.load(path)
+        assert ei.value.status == lbm.LBM_E_IO
+    a.close()
+    b.close()
+
+
+def test_error_paths(lbm):
+    p = inputs.tgv_params(8)
+    dom = lbm.Domain(p)
+    with pytest.raises(lbm.LbmError) as ei:
+        dom.step(1)
+    assert ei.value.status == lbm.LBM_E_STATE
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.step(0)
+    f = dom.populations()
+    f[0, 0, 3, 2, 1] = np.nan  # a corrupted population on the host side
+    dom.set_populations(f)
+    dom.step(2)
+    with pytest.raises(lbm.LbmError) as ei:
+        dom.synchronize()
+    assert ei.value.status == lbm.LBM_E_NONFINITE
+    with pytest.raises(lbm.LbmError) as ei:
+        dom.step(1)
+    assert ei.value.status == lbm.LBM_E_NONFINITE
+    d = dom.diag()
+    assert d["status"] == lbm.LBM_E_NONFINITE and d["nonfinite"] > 0
+    dom.init_tgv(1.0, 1.25, 1.0)  # re-init clears the flag
+    dom.step(2)
+    dom.synchronize()
+    dom.close()
