@@ -1,0 +1,424 @@
+"""Benchmark of the fused compressible-NSF D3Q7 time step (supersonic TGV, 512^3).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--n 512] [--store f32] [--impl reference]
+
+One step = one pass of the whole hot path over the grid: per cell, load 98
+populations, moments, closure, sensor, collision, store 98 populations in place
+(one kernel launch, replayed from CUDA graphs). Inputs (52.6 GB of populations
+at 512^3 FP32) are far larger than the 129 MB L2, so no flush is needed between
+steps. Prints one JSON line (rank 0).
+
+Multi-GPU: the path has no exchange step between independent problems here, so
+N ranks run N replicas (weak scaling): barrier + synchronize around the timed
+region, the max time over ranks, value = all ranks' cell updates / that time.
+
+--impl reference times the FP64 CPU oracle on host cores on a bounded sample of
+the same workload (a window of the 512^3 TGV per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and achieved HBM GB/s vs peak, 512^3 TGV; FP32 vs FP16-store at stated err"
+BYTES_PER_CELL = {"f32": 784, "f16": 392, "bf16": 392}
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ("paper_2608_13437_gb300/csrc/lbm_device.cuh",
+                  "paper_2608_13437_gb300/csrc/step_impl.cuh")
+
+
+def workload_name(n):
+    return (f"supersonic Taylor-Green vortex {n}^3 periodic [0,2pi)^3, gamma 1.4, Pr 0.71, M0 1.25, "
+            "Re 1000, uniform T0, Sutherland, C_sigma 40, J_min 1e-2, omega_min 1.987, "
+            "tau_R = tau_q = 5e-3, CFL 0.1, 14 fields x D3Q7, in-place AA streaming")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(store, ncell):
+    """DRAM bytes per launch from the committed ncu summary, scaled by cells; None
+    when the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    ent = d.get(store)
+    if not ent or ent.get("kernel_hash") != kernel_hash():
+        return None
+    return ent["dram_bytes_per_cell"] * ncell
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def time_oracle(n_global, side, steps, warmup, threads=None):
+    """Runs the FP64 oracle on a side^3 window of the n_global^3 TGV; returns
+    (MLUPS, seconds, threads)."""
+    from oracle.oracle import Oracle, get_threads, set_threads
+    from paper_2608_13437_gb300 import inputs
+    if threads:
+        set_threads(threads)
+    p = inputs.tgv_params(n_global)
+    p.update(nx=side, ny=side, nz=side)
+    q = dict(p)
+    o = Oracle(q.pop("nx"), q.pop("ny"), q.pop("nz"), q.pop("dx"), **q)
+    o.init_tgv(1.0, 1.25, 1.0, gn=n_global, origin=(0, 0, 0))
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return side ** 3 * steps / dt / 1e6, dt, get_threads()
+
+
+def cpu_baseline(n_global, budget_s=15.0):
+    """Bounded sample: calibrate on 32^3, then time a 128^3 window for as many steps
+    as fit in about budget_s seconds."""
+    rate, _, thr = time_oracle(n_global, 32, 2, 0)
+    side = 128
+    steps = max(1, min(50, int(budget_s * rate * 1e6 / side ** 3)))
+    mlups, secs, thr = time_oracle(n_global, side, steps, 0)
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+            "sample": f"FP64 oracle, {side}^3 window of the {n_global}^3 TGV, {steps} steps "
+                      f"({secs:.1f} s), OpenMP over z-planes"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    rate, _, thr = time_oracle(args.n, 32, 2, 0)
+    total = args.steps + args.warmup
+    side = int((90.0 * rate * 1e6 / max(total, 1)) ** (1.0 / 3.0))
+    side = max(8, min(side, 160))
+    mlups, secs, thr = time_oracle(args.n, side, args.steps, args.warmup)
+    ms = secs * 1e3 / max(args.steps, 1)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "n": args.n, "store": "f64 (oracle)",
+                   "sample_per_step": f"{side}^3 window"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+                         "sample": f"FP64 oracle on a {side}^3 window of the {args.n}^3 TGV per step"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def stated_error(store, n=32, steps=100):
+    """rel-L2 of rho, u, T against the FP64 oracle after `steps` TGV steps at n^3."""
+    import numpy as np
+
+    from oracle.oracle import Oracle
+    from paper_2608_13437_gb300 import inputs, lbm
+    p = inputs.tgv_params(n)
+    d = lbm.Domain(p, store=store)
+    d.init_tgv(1.0, 1.25, 1.0)
+    d.step(steps)
+    g = d.primitives()
+    d.close()
+    q = dict(p)
+    o = Oracle(q.pop("nx"), q.pop("ny"), q.pop("nz"), q.pop("dx"), **q)
+    o.init_tgv(1.0, 1.25, 1.0)
+    o.step(steps)
+    r = o.primitives()
+
+    def rel(a, b):
+        return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+    return {"rho": rel(g[0], r[0]), "u": rel(g[1:4], r[1:4]), "T": rel(g[4], r[4]),
+            "case": f"TGV {n}^3, {steps} steps, vs FP64 oracle"}
+
+
+def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
+    stream = dom.stream
+    dom.step(warmup)
+    dom.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(sampler_index) if sampler_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    a.record(stream)
+    dom.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+        clocks = sampler.summary()
+    if dist:
+        dist.barrier()
+    ms = a.elapsed_time(b)
+    dom.synchronize()
+    return ms, clocks
+
+
+def batch_leg(torch, lbm, inputs, steps, warmup):
+    """64 independent TGV domains (sizes, M0, Re from SplitMix64(0)): one persistent
+    launch per step (CUDA graph, autotuned tiles) against 64 plain launches per step."""
+    doms = inputs.batch_domains()
+    pl = inputs.batch_params(doms)
+    B = lbm.Batch([q for q, _ in pl])
+    ic = [[c["U0"] for _, c in pl], [c["M0"] for _, c in pl], [c["rho0"] for _, c in pl]]
+    B.init_tgv(*ic)
+    tune = B.autotune(4)
+    cells = B.total_cells()
+    out = {"domains": len(doms), "cells": cells, "tune": tune}
+    for name, fn in (("persistent", B.step), ("sequential", B.step_sequential)):
+        B.init_tgv(*ic)
+        fn(warmup)
+        B.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(B.stream)
+        fn(steps)
+        b.record(B.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        B.synchronize()
+        out[name] = {"value": round(cells / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                     "ms_per_step": round(ms, 4),
+                     "achieved_gbs": round(784 * cells / (ms * 1e-3) / 1e9, 1)}
+    B.close()
+    return out
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2608_13437_gb300 import inputs, lbm
+
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    n = args.n
+    ncell = n ** 3
+    p = inputs.tgv_params(n)
+    dom = lbm.Domain(p, store=args.store)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    tune = dom.autotune(pairs_per_trial=3)   # advances the state: re-init below
+    dom.init_tgv(1.0, 1.25, 1.0)
+    ms_total, clocks = time_steps(torch, dom, args.steps, args.warmup, dist,
+                                  sampler_index=dev if rank == 0 else None)
+    ms_max = ms_total
+    if dist:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+    hbm, peak_kind = peaks()
+    bpc = BYTES_PER_CELL[args.store]
+    achieved = bpc * ncell / (ms_total / args.steps * 1e-3) / 1e9
+    traffic = traffic_per_launch(args.store, ncell)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpc * ncell}
+
+    # end to end through the C ABI: host fields in, K steps with the FP64 diagnostic
+    # time series read back every 50 steps, host primitives out.
+    fields = torch.from_numpy(inputs.tgv_fields(n, dtype=np.float32)).pin_memory()
+    out = torch.empty((6, n, n, n), dtype=torch.float32).pin_memory()
+    diag_every = 50
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dom.init_fields_device(fields, src_on_device=False)
+    series = []
+    done = 0
+    while done < args.steps:
+        k = min(diag_every, args.steps - done)
+        dom.step(k)
+        done += k
+        if done % diag_every == 0 or done == args.steps:
+            series.append(dom.diag())
+    dom.moments_into(out, which=lbm.MOM_PRIM, on_device=False)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * ncell * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(fields.numel() * 4 / args.steps),
+           "d2h_bytes_per_step": int((out.numel() * 4 + len(series) * 15 * 8) / args.steps),
+           "api": "lbm_init_fields(host) + lbm_step + lbm_diag every 50 steps + lbm_moments(host)",
+           "ek_final": series[-1]["ek_mean"] if series else None}
+    dom.close()
+    del dom, fields, out
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for st in ("f16", "bf16"):
+            if st == args.store:
+                continue
+            d2 = lbm.Domain(p, store=st)
+            d2.init_tgv(1.0, 1.25, 1.0)
+            k2 = max(10, min(args.steps, 400))
+            ms2, _ = time_steps(torch, d2, k2, max(args.warmup, 3))
+            d2.close()
+            del d2
+            torch.cuda.empty_cache()
+            ach = BYTES_PER_CELL[st] * ncell / (ms2 / k2 * 1e-3) / 1e9
+            variants[st] = {"value": round(ncell * k2 / (ms2 * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                            "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4),
+                            "steps": k2, "stated_err": stated_error(st)}
+        variants[args.store] = {"stated_err": stated_error(args.store), "tune": tune}
+        variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
+
+    cpu = cpu_baseline(n) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(n), "n": n, "cells": ncell, "store": args.store,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "populations (%.1f GB) exceed the 129 MB L2; no flush between steps"
+                             % (BYTES_PER_CELL[args.store] / 2 * ncell / 1e9)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--store", default="f32", choices=("f32", "f16", "bf16"))
+    ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    from paper_2608_13437_gb300 import build
+    build.build()
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,8 @@ typedef struct {
   size_t population_bytes;  /* bytes of the population buffer */
   int store;
   int block_x;              /* threads per block of the step kernel */
+  int variant;              /* register budget of the step kernel: 0 = 3 blocks of 128
+                               threads per SM (<= 170 registers), 1 = 4 blocks (<= 128) */
 } lbm_info_t;
 
 /* Diagnostics (Sec. 3.2, Eq. 7). Sums and extrema in FP64 over all cells.
@@ -135,15 +137,16 @@ typedef struct {
 /* Kernel configuration chosen by the autotuner. */
 typedef struct {
   int block_x;          /* threads per block of the step kernel */
+  int variant;          /* register budget (see lbm_info_t) */
   float ms_per_step;    /* measured time of one step with that configuration */
   int candidates;       /* configurations timed */
 } lbm_tune_t;
 
 /* ---- lifecycle -------------------------------------------------------------- */
 
-/* Bytes of the population buffer for these parameters: 98 arrays (14 fields x 7
- * directions) of nx*ny*nz elements of the storage type, each array starting on a
- * 256-byte boundary. Returns 0 if the sizes are invalid. */
+/* Bytes of the population buffer for these parameters: ceil(cells / 32) tiles of
+ * 98 x 32 elements of the storage type (tiled SoA: a tile holds the 98 arrays
+ * (field, direction) of 32 consecutive cells). Returns 0 if the sizes are invalid. */
 size_t lbm_population_bytes(const lbm_params* p);
 
 /* Validates *p (LBM_E_INVAL with the reason), derives dt and the relaxation
@@ -244,19 +247,27 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 
 /* ---- tuning ------------------------------------------------------------------- */
 
-/* Times the step kernel for each candidate block size (whole step pairs, CUDA
- * events on the handle's stream) and keeps the fastest in the handle; returns it
- * in *out if out != NULL. Each candidate runs on the live state, so the state
- * advances by an even number of steps: call it before init, or re-init after. */
+/* Times the step kernel for each candidate block size and register budget (whole
+ * step pairs, CUDA events on the handle's stream) and keeps the fastest in the
+ * handle; returns it in *out if out != NULL. Needs an initialised state
+ * (LBM_E_STATE otherwise); each candidate runs on the live state, so the state
+ * advances by an even number of steps: re-init before the run you keep. */
 lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
+
+/* Fixes the step kernel's block size (32, 64, 96 or 128 threads) and register budget
+ * (variant 0 or 1, see lbm_info_t) instead of the defaults or the autotuner's choice.
+ * All configurations compute bit-identical populations. */
+lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
 
 /* ---- many independent domains (batched mode) -------------------------------------
  * n periodic domains with their own sizes and parameters (F32 storage), stored in
  * one buffer. lbm_batch_step advances all of them by one step per persistent launch
- * (grid = resident blocks of the GPU, blocks take work tiles from a table ordered
- * largest domain first), replayed from a CUDA graph; lbm_batch_step_sequential
- * issues one plain launch per domain per step instead (same arithmetic, for
- * comparison). Tile size and block size come from lbm_batch_autotune. */
+ * (grid = the resident blocks of the GPU; each warp takes items of consecutive
+ * 32-cell tiles across all domains, the domain constants staged in shared memory),
+ * replayed from a CUDA graph; lbm_batch_step_sequential issues one plain launch per
+ * domain per step instead. Both give bit-identical populations. Items per warp,
+ * block size and register budget come from lbm_batch_autotune. At most a few
+ * hundred domains per batch (their constants must fit in shared memory). */
 lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out);
 lbm_status lbm_batch_destroy(lbm_batch* b);
 /* Per-domain TGV parameters, arrays of n values (host). */
@@ -270,8 +281,10 @@ lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int
                              int dtype);
 /* Total cells of all domains; time step of one domain. */
 lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain, double* dt);
-/* Times tile sizes x block sizes of the persistent kernel and keeps the fastest;
- * advances the state like lbm_autotune. out may be NULL. */
+/* Times items per warp (1, 2, 4, 8 tiles of 32 cells) x block sizes x register
+ * budgets of the persistent kernel and keeps the fastest; reports the cells per item,
+ * the block size and the time per step (each pointer may be NULL). Advances the
+ * state like lbm_autotune. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells,
                               int* block_threads, float* ms_per_step);
 

@@ -28,11 +28,7 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
 
 size_t elem_size(int store) { return store == LBM_STORE_F32 ? 4 : 2; }
 
-long long padded_stride(long long ncell, int store) {
-  const long long e = (long long)elem_size(store);
-  const long long bytes = ((ncell * e + 255) / 256) * 256;
-  return bytes / e;
-}
+long long tile_count(long long ncell) { return (ncell + kTile - 1) / kTile; }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
@@ -82,7 +78,7 @@ void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, Doma
   P->nz = p->nz;
   P->bc_x = p->bc_x;
   P->ncell = (long long)p->nx * p->ny * p->nz;
-  P->stride = padded_stride(P->ncell, p->store);
+  P->ntile = tile_count(P->ncell);
   const double c = p->dx / dt;
   P->c = (float)c;
   P->inv_c = (float)(1.0 / c);
@@ -113,11 +109,11 @@ void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, Doma
 }
 
 cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, const float* ghost,
-                        unsigned* flag, int block_x, cudaStream_t s) {
+                        unsigned* flag, int block_x, int variant, cudaStream_t s) {
   switch (store) {
-    case LBM_STORE_F32: return launch_step_f32(P, parity, pop, ghost, flag, block_x, s);
-    case LBM_STORE_F16: return launch_step_f16(P, parity, pop, ghost, flag, block_x, s);
-    default: return launch_step_bf16(P, parity, pop, ghost, flag, block_x, s);
+    case LBM_STORE_F32: return launch_step_f32(P, parity, pop, ghost, flag, block_x, variant, s);
+    case LBM_STORE_F16: return launch_step_f16(P, parity, pop, ghost, flag, block_x, variant, s);
+    default: return launch_step_bf16(P, parity, pop, ghost, flag, block_x, variant, s);
   }
 }
 
@@ -142,7 +138,8 @@ struct lbm_handle {
   long long step = 0;
   bool initialized = false;
   bool nonfinite = false;
-  int block_x = 128;
+  int block_x = 64;
+  int variant = 0;             // register budget of the step kernel (see launch_step_t)
   cudaGraphExec_t g_pair = nullptr, g_chunk = nullptr;
   bool graphs_valid = false;
   double* ufield = nullptr;
@@ -179,7 +176,8 @@ lbm_status capture(lbm_handle* h, int pairs, cudaGraphExec_t* out) {
   LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int j = 0; j < 2 * pairs && le == cudaSuccess; ++j)
-    le = launch_step(h->P, h->prm.store, j & 1, h->pop, h->ghost, h->flag, effective_block(h), h->cap);
+    le = launch_step(h->P, h->prm.store, j & 1, h->pop, h->ghost, h->flag, effective_block(h),
+                     h->variant, h->cap);
   cudaError_t ee = cudaStreamEndCapture(h->cap, &g);
   if (le != cudaSuccess || ee != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -205,7 +203,7 @@ lbm_status ensure_graphs(lbm_handle* h) {
 
 lbm_status direct_step(lbm_handle* h) {
   LBM_CUDA(launch_step(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->ghost, h->flag,
-                       effective_block(h), h->stream));
+                       effective_block(h), h->variant, h->stream));
   h->step += 1;
   return LBM_OK;
 }
@@ -272,7 +270,7 @@ size_t lbm_population_bytes(const lbm_params* p) {
   if (!p || p->nx < 1 || p->ny < 1 || p->nz < 1 || p->store < 0 || p->store > 2) return 0;
   const long long n = (long long)p->nx * p->ny * p->nz;
   if (n >= (1LL << 31)) return 0;
-  return (size_t)padded_stride(n, p->store) * elem_size(p->store) * kP;
+  return (size_t)tile_count(n) * kP * kTile * elem_size(p->store);
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -304,6 +302,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
     return fail(LBM_E_INVAL, "derived dt is not a positive finite number");
   }
   fill_const(p, h->dt, h->tau_R, h->tau_q, &h->P);
+  // Measured on GB300 at 512^3: blocks of 64 threads; the 170-register budget for
+  // FP32 storage, the 128-register budget for 16-bit storage (lbm_autotune re-times).
+  h->block_x = 64;
+  h->variant = p->store == LBM_STORE_F32 ? 0 : 1;
   h->ncell = h->P.ncell;
   h->pop_bytes = lbm_population_bytes(p);
   for (int k = 0; k < kF; ++k) h->scale[k] = 1.0;
@@ -371,6 +373,7 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out) {
   out->population_bytes = h->pop_bytes;
   out->store = h->prm.store;
   out->block_x = effective_block(h);
+  out->variant = h->variant;
   return LBM_OK;
 }
 
@@ -654,45 +657,61 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
   if (!h->initialized) return fail(LBM_E_STATE, "autotune needs an initialised state");
   if (pairs_per_trial < 1) pairs_per_trial = 4;
-  const int cands[] = {64, 128, 256};
+  const int blocks[] = {64, 128};
+  const int variants[] = {0, 1};
   cudaEvent_t a, b;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
-  int best_b = h->block_x, tried = 0;
-  for (int cb : cands) {
-    if (cb > 32 * ((h->P.nx + 31) / 32) && cb != cands[0]) continue;
-    h->block_x = cb;
-    // warm-up pair, then the timed pairs
-    for (int j = 0; j < 2; ++j)
-      LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
-                           effective_block(h), h->stream));
-    h->step += 2;
-    LBM_CUDA(cudaEventRecord(a, h->stream));
-    for (int j = 0; j < 2 * pairs_per_trial; ++j)
-      LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
-                           effective_block(h), h->stream));
-    h->step += 2 * pairs_per_trial;
-    LBM_CUDA(cudaEventRecord(b, h->stream));
-    LBM_CUDA(cudaEventSynchronize(b));
-    float ms = 0;
-    LBM_CUDA(cudaEventElapsedTime(&ms, a, b));
-    ms /= (float)(2 * pairs_per_trial);
-    ++tried;
-    if (ms < best) {
-      best = ms;
-      best_b = cb;
+  int best_b = h->block_x, best_v = h->variant, tried = 0;
+  for (int cv : variants)
+    for (int cb : blocks) {
+      if (cb > 32 * ((h->P.nx + 31) / 32) && cb != blocks[0]) continue;
+      h->block_x = cb;
+      h->variant = cv;
+      for (int j = 0; j < 2; ++j)  // warm-up pair
+        LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
+                             effective_block(h), h->variant, h->stream));
+      h->step += 2;
+      LBM_CUDA(cudaEventRecord(a, h->stream));
+      for (int j = 0; j < 2 * pairs_per_trial; ++j)
+        LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
+                             effective_block(h), h->variant, h->stream));
+      h->step += 2 * pairs_per_trial;
+      LBM_CUDA(cudaEventRecord(b, h->stream));
+      LBM_CUDA(cudaEventSynchronize(b));
+      float ms = 0;
+      LBM_CUDA(cudaEventElapsedTime(&ms, a, b));
+      ms /= (float)(2 * pairs_per_trial);
+      ++tried;
+      if (ms < best) {
+        best = ms;
+        best_b = cb;
+        best_v = cv;
+      }
     }
-  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->block_x = best_b;
+  h->variant = best_v;
   h->graphs_valid = false;
   if (out) {
     out->block_x = effective_block(h);
+    out->variant = best_v;
     out->ms_per_step = best;
     out->candidates = tried;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
+  if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  if (block_x < 32 || block_x > 128 || (block_x & 31))
+    return fail(LBM_E_INVAL, "block_x must be 32, 64, 96 or 128");
+  if (variant < 0 || variant > 1) return fail(LBM_E_INVAL, "variant must be 0 or 1");
+  h->block_x = block_x;
+  h->variant = variant;
+  h->graphs_valid = false;
   return LBM_OK;
 }
 

@@ -11,12 +11,12 @@ namespace lbm {
 extern thread_local std::string g_last_error;
 lbm_status fail(lbm_status s, const char* fmt, ...);
 size_t elem_size(int store);
-long long padded_stride(long long ncell, int store);
+long long tile_count(long long ncell);
 lbm_status validate(const lbm_params* p);
 void derive(const lbm_params* p, double* dt, double* tau_R, double* tau_q);
 void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, DomainConst* P);
 cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, const float* ghost,
-                        unsigned* flag, int block_x, cudaStream_t s);
+                        unsigned* flag, int block_x, int variant, cudaStream_t s);
 bool finite_pos(double v);
 
 }  // namespace lbm

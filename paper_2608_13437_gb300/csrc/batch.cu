@@ -1,11 +1,13 @@
 // Batched mode: many independent periodic domains of different sizes and
 // parameters, stored in one buffer, advanced by ONE persistent launch per time
-// step. The grid holds as many blocks as are resident on the GPU; block b takes
-// tiles b, b + grid, b + 2 grid, ... of a table ordered largest domain first. A
-// tile is `tile_cells` consecutive cells of one domain; the block stages that
-// domain's constants in shared memory and runs the same per-cell update as the
-// single-domain kernel. Tile and block sizes come from the autotuner; the step
-// pair is replayed from a CUDA graph.
+// step. The grid holds as many blocks as are resident on the GPU. Each block
+// stages every domain's constants in shared memory once; then each warp works on
+// its own items, an item being `tiles_per_item` consecutive 32-cell layout tiles
+// (warp w takes items w, w + warps, ...). A tile's domain is found by binary search
+// in the per-domain tile prefix sums; no block-wide synchronisation happens after
+// the staging, so warps overlap their loads and arithmetic freely. The per-cell
+// update is the single-domain one. Items per warp, block size and register budget
+// come from the autotuner; the step pair is replayed from a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,39 +21,63 @@ using namespace lbm;
 namespace lbm {
 namespace {
 
-struct Tile {
-  int domain;
-  int first;  // first cell of the tile within its domain
-};
-
-template <int PARITY>
-__global__ void __launch_bounds__(256) k_batch_step(const DomainConst* __restrict__ consts,
-                                                    float* const* __restrict__ pops,
-                                                    const Tile* __restrict__ tiles, int ntiles,
-                                                    int tile_cells, unsigned* __restrict__ flag) {
-  __shared__ DomainConst sP;
-  __shared__ float* sPop;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tile = tiles[t];
-    __syncthreads();  // previous tile's readers are done with sP
-    if (threadIdx.x == 0) {
-      sP = consts[tile.domain];
-      sPop = pops[tile.domain];
-    }
-    __syncthreads();
-    const DomainConst& P = sP;
-    float* pop = sPop;
-    const long long end = min((long long)tile.first + tile_cells, P.ncell);
-    for (long long cell = tile.first + threadIdx.x; cell < end; cell += blockDim.x) {
-      const int x = (int)(cell % P.nx);
-      const long long yz = cell / P.nx;
-      const CellIndex c = make_index(P, x, (int)(yz % P.ny), (int)(yz / P.ny));
+template <int PARITY, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
+                                                          float* const* __restrict__ pops,
+                                                          const int* __restrict__ tile_prefix,
+                                                          int ndom, int total_tiles,
+                                                          int tiles_per_item,
+                                                          unsigned* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  DomainConst* sP = reinterpret_cast<DomainConst*>(smem);
+  float** sPop = reinterpret_cast<float**>(sP + ndom);
+  int* sPrefix = reinterpret_cast<int*>(sPop + ndom);
+  {
+    const int words = ndom * (int)(sizeof(DomainConst) / 4);
+    const int* src = reinterpret_cast<const int*>(consts);
+    int* dst = reinterpret_cast<int*>(sP);
+    for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
+    for (int j = threadIdx.x; j < ndom; j += blockDim.x) sPop[j] = pops[j];
+    for (int j = threadIdx.x; j <= ndom; j += blockDim.x) sPrefix[j] = tile_prefix[j];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int item = warp; item * tiles_per_item < total_tiles; item += nwarps) {
+    const int t_end = min(total_tiles, (item + 1) * tiles_per_item);
+    for (int t = item * tiles_per_item; t < t_end; ++t) {
+      int lo = 0, hi = ndom;  // sPrefix[lo] <= t < sPrefix[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sPrefix[mid] <= t) lo = mid;
+        else hi = mid;
+      }
+      const DomainConst& P = sP[lo];
+      const int first = (t - sPrefix[lo]) * kTile;
+      const int cell = first + lane;
+      if (cell >= P.ncell) continue;
+      // (x, y, z) of the tile's first cell (one division per tile), then this lane's
+      // by carrying x past the row end (several rows when nx < 32).
+      const unsigned yz0 = (unsigned)first / (unsigned)P.nx;
+      const unsigned z0 = yz0 / (unsigned)P.ny;
+      int x = first - (int)yz0 * P.nx + lane;
+      int y = (int)(yz0 - z0 * (unsigned)P.ny);
+      int z = (int)z0;
+      while (x >= P.nx) {
+        x -= P.nx;
+        if (++y == P.ny) {
+          y = 0;
+          ++z;
+        }
+      }
+      const CellIndex c = make_index(P, x, y, z);
+      float* pop = sPop[lo];
       float d[kF][kQ];
       load_cell<PARITY, false, float>(P, pop, nullptr, c, d);
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
-#pragma unroll
-      for (int k = 0; k < kF; ++k) store_field<PARITY, float>(P, pop, c, k, d[k]);
+      store_cell<PARITY, float>(P, pop, c, d);
     }
   }
 }
@@ -69,11 +95,13 @@ struct lbm_batch {
   void* pool = nullptr;
   DomainConst* d_consts = nullptr;
   float** d_pops = nullptr;
-  Tile* d_tiles = nullptr;
-  int ntiles = 0;
-  int tile_cells = 1024;
-  int block = 128;
+  int* d_prefix = nullptr;     // per-domain prefix sums of 32-cell tiles (n + 1)
+  int total_tiles = 0;
+  int tiles_per_item = 4;      // layout tiles a warp takes at a time
+  int block = 64;
+  int variant = 0;             // register budget: 0 -> 3, 1 -> 4 blocks of 128 per SM
   int grid = 0;
+  size_t smem = 0;
   unsigned* flag = nullptr;
   float* ghost = nullptr;  // unused by periodic domains; a valid pointer for the plain kernel
   cudaStream_t stream = nullptr;
@@ -98,38 +126,42 @@ float* domain_pop(lbm_batch* b, int d) {
   return reinterpret_cast<float*>(static_cast<char*>(b->pool) + b->offset[d]);
 }
 
-// Tile table, largest domain first; rebuilt when tile_cells changes.
-lbm_status build_tiles(lbm_batch* b) {
-  std::vector<int> order(b->n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int c) { return b->P[a].ncell > b->P[c].ncell; });
-  std::vector<Tile> tiles;
-  for (int d : order)
-    for (long long f = 0; f < b->P[d].ncell; f += b->tile_cells) tiles.push_back(Tile{d, (int)f});
-  if (b->d_tiles) cudaFree(b->d_tiles);
-  b->d_tiles = nullptr;
-  LBM_CUDA(cudaMalloc(&b->d_tiles, sizeof(Tile) * tiles.size()));
-  LBM_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
-  b->ntiles = (int)tiles.size();
+template <int P, int M>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(k_batch_step<P, M>);
+}
+
+// Grid size for the current block size and register budget: every block resident.
+lbm_status size_grid(lbm_batch* b) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<0>, b->block, 0);
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  void* fn = b->variant ? kernel_ptr<0, 4>() : kernel_ptr<0, 3>();
+  if (b->smem > 48 * 1024) {
+    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<0, 3>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<1, 3>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<0, 4>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<1, 4>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, b->smem);
+  if (e != cudaSuccess || per_sm < 1) return fail(LBM_E_CUDA, "batched kernel does not fit on an SM");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid = std::max(1, std::min(per_sm * sms, b->ntiles));
+  const int warps_needed = (b->total_tiles + b->tiles_per_item - 1) / b->tiles_per_item;
+  const int blocks_needed = (warps_needed * 32 + b->block - 1) / b->block;
+  b->grid = std::max(1, std::min(per_sm * sms, blocks_needed));
   b->graphs_valid = false;
   return LBM_OK;
 }
 
 cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t s) {
-  if (parity)
-    k_batch_step<1><<<b->grid, b->block, 0, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->ntiles,
-                                                   b->tile_cells, b->flag);
-  else
-    k_batch_step<0><<<b->grid, b->block, 0, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->ntiles,
-                                                   b->tile_cells, b->flag);
+  const dim3 g(b->grid), bl(b->block);
+  if (b->variant) {
+    if (parity) k_batch_step<1, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+    else k_batch_step<0, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+  } else {
+    if (parity) k_batch_step<1, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+    else k_batch_step<0, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+  }
   return cudaGetLastError();
 }
 
@@ -194,7 +226,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     b->rho_ref.push_back(0.0);
     b->E_ref.push_back(0.0);
     b->offset.push_back(bytes);
-    bytes += (size_t)P.stride * sizeof(float) * kP;
+    bytes += (size_t)P.ntile * kP * kTile * sizeof(float);
     b->total_cells += P.ncell;
   }
   b->stream = static_cast<cudaStream_t>(params[0].cuda_stream);
@@ -209,18 +241,25 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   }
   std::vector<float*> ptrs(n);
   for (int d = 0; d < n; ++d) ptrs[d] = domain_pop(b, d);
+  std::vector<int> prefix(n + 1, 0);
+  for (int d = 0; d < n; ++d) prefix[d + 1] = prefix[d] + (int)b->P[d].ntile;
+  b->total_tiles = prefix[n];
+  b->smem = sizeof(DomainConst) * n + sizeof(float*) * n + sizeof(int) * (n + 1);
+  if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pops, sizeof(float*) * n) != cudaSuccess ||
+      cudaMalloc(&b->d_prefix, sizeof(int) * (n + 1)) != cudaSuccess ||
       cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
   }
   if (cudaMemcpy(b->d_pops, ptrs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "batch table upload failed"));
   lbm_status s = upload_consts(b);
   if (s != LBM_OK) return cleanup(s);
-  s = build_tiles(b);
+  s = size_grid(b);
   if (s != LBM_OK) return cleanup(s);
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "cudaStreamCreate failed"));
@@ -235,7 +274,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->pool) cudaFree(b->pool);
   if (b->d_consts) cudaFree(b->d_consts);
   if (b->d_pops) cudaFree(b->d_pops);
-  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_prefix) cudaFree(b->d_prefix);
   if (b->flag) cudaFree(b->flag);
   if (b->ghost) cudaFree(b->ghost);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -314,7 +353,7 @@ lbm_status lbm_batch_step_sequential(lbm_batch* b, int n) {
     const int parity = (int)(b->step & 1);
     for (int d = 0; d < b->n; ++d) {
       const int bx = std::min(128, ((b->P[d].nx + 31) / 32) * 32);
-      LBM_CUDA(launch_step(b->P[d], LBM_STORE_F32, parity, domain_pop(b, d), b->ghost, b->flag, bx,
+      LBM_CUDA(launch_step(b->P[d], LBM_STORE_F32, parity, domain_pop(b, d), b->ghost, b->flag, bx, 1,
                            b->stream));
     }
     b->step += 1;
@@ -373,45 +412,50 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells
                               float* ms_per_step) {
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
   if (!b->initialized) return fail(LBM_E_STATE, "autotune needs an initialised batch");
-  if (steps_per_trial < 2) steps_per_trial = 4;
+  if (steps_per_trial < 2) steps_per_trial = 8;
   steps_per_trial += steps_per_trial & 1;  // whole pairs keep the parity
-  const int tiles[] = {256, 512, 1024, 2048, 4096};
-  const int blocks[] = {128, 256};
+  const int items[] = {1, 2, 4, 8};
+  const int blocks[] = {64, 128};
+  const int variants[] = {0, 1};
   cudaEvent_t a, e;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&e));
   float best = 1e30f;
-  int best_t = b->tile_cells, best_b = b->block;
-  for (int bl : blocks)
-    for (int tc : tiles) {
-      b->block = bl;
-      b->tile_cells = tc;
-      lbm_status s = build_tiles(b);
-      if (s != LBM_OK) return s;
-      for (int j = 0; j < 2; ++j) LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
-      b->step += 2;
-      LBM_CUDA(cudaEventRecord(a, b->stream));
-      for (int j = 0; j < steps_per_trial; ++j)
-        LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
-      b->step += steps_per_trial;
-      LBM_CUDA(cudaEventRecord(e, b->stream));
-      LBM_CUDA(cudaEventSynchronize(e));
-      float ms = 0;
-      LBM_CUDA(cudaEventElapsedTime(&ms, a, e));
-      ms /= (float)steps_per_trial;
-      if (ms < best) {
-        best = ms;
-        best_t = tc;
-        best_b = bl;
+  int best_i = b->tiles_per_item, best_b = b->block, best_v = b->variant;
+  for (int v : variants)
+    for (int bl : blocks)
+      for (int it : items) {
+        b->variant = v;
+        b->block = bl;
+        b->tiles_per_item = it;
+        lbm_status s = size_grid(b);
+        if (s != LBM_OK) return s;
+        for (int j = 0; j < 2; ++j) LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
+        b->step += 2;
+        LBM_CUDA(cudaEventRecord(a, b->stream));
+        for (int j = 0; j < steps_per_trial; ++j)
+          LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
+        b->step += steps_per_trial;
+        LBM_CUDA(cudaEventRecord(e, b->stream));
+        LBM_CUDA(cudaEventSynchronize(e));
+        float ms = 0;
+        LBM_CUDA(cudaEventElapsedTime(&ms, a, e));
+        ms /= (float)steps_per_trial;
+        if (ms < best) {
+          best = ms;
+          best_i = it;
+          best_b = bl;
+          best_v = v;
+        }
       }
-    }
   cudaEventDestroy(a);
   cudaEventDestroy(e);
+  b->tiles_per_item = best_i;
   b->block = best_b;
-  b->tile_cells = best_t;
-  lbm_status s = build_tiles(b);
+  b->variant = best_v;
+  lbm_status s = size_grid(b);
   if (s != LBM_OK) return s;
-  if (tile_cells) *tile_cells = best_t;
+  if (tile_cells) *tile_cells = best_i * kTile;
   if (block_threads) *block_threads = best_b;
   if (ms_per_step) *ms_per_step = best;
   return LBM_OK;

@@ -90,7 +90,7 @@ __global__ void k_init(const DomainConst P, const InitSpec sp, int mode, S* __re
     }
     for (int k = 0; k < kF; ++k)
       for (int i = 0; i < kQ; ++i)
-        pop[(long long)(k * kQ + i) * P.stride + cell] = Codec<S>::enc((float)dev[k][i], P.inv_scale[k]);
+        pop[pop_index(cell, k, i)] = Codec<S>::enc((float)dev[k][i], P.inv_scale[k]);
     if (P.bc_x && ghost) {
       const long long plane = yz;
       if (x == 0)

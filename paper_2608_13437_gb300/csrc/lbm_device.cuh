@@ -31,7 +31,7 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 struct DomainConst {
   int nx, ny, nz, bc_x;
   long long ncell;
-  long long stride;   // elements between consecutive population arrays (>= ncell)
+  long long ntile;    // 32-cell tiles of the population buffer
   float c, inv_c, half_inv_c, dt;
   float gm1;          // gamma - 1
   float gamma;
@@ -49,18 +49,88 @@ struct DomainConst {
 };
 
 // ---------------------------------------------------------------- storage codecs
+// Scalar codecs (dec/enc) and the vector forms used by the step kernel: V4 holds
+// four consecutive fields of one direction of one cell, V2 two.
 template <typename S>
 struct Codec;
 
 template <>
 struct Codec<float> {
+  using V4 = float4;
+  using V2 = float2;
   static __device__ __forceinline__ float dec(float g, float) { return g; }
   static __device__ __forceinline__ float enc(float d, float) { return d; }
   static __device__ __forceinline__ double dec64(float g, double) { return (double)g; }
+  static __device__ __forceinline__ void dec4(const V4& v, const float*, float o[4]) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void dec2(const V2& v, const float*, float o[2]) {
+    o[0] = v.x; o[1] = v.y;
+  }
+  static __device__ __forceinline__ V4 enc4(const float i[4], const float*) {
+    return make_float4(i[0], i[1], i[2], i[3]);
+  }
+  static __device__ __forceinline__ V2 enc2(const float i[2], const float*) {
+    return make_float2(i[0], i[1]);
+  }
+};
+
+// 16-bit codecs: pairs of values travel as one 32-bit word.
+template <typename H, typename H2>
+struct Codec16 {
+  using V4 = uint2;
+  using V2 = unsigned;
+  static __device__ __forceinline__ float2 to_f2(unsigned w);
+  static __device__ __forceinline__ unsigned from_f2(float a, float b);
+  static __device__ __forceinline__ void dec2w(unsigned w, const float* s, float* o) {
+    const float2 f = to_f2(w);
+    o[0] = f.x * s[0];
+    o[1] = f.y * s[1];
+  }
+  static __device__ __forceinline__ void dec4(const V4& v, const float* s, float o[4]) {
+    dec2w(v.x, s, o);
+    dec2w(v.y, s + 2, o + 2);
+  }
+  static __device__ __forceinline__ void dec2(const V2& v, const float* s, float o[2]) {
+    dec2w(v, s, o);
+  }
+  static __device__ __forceinline__ V4 enc4(const float i[4], const float* is) {
+    return make_uint2(from_f2(i[0] * is[0], i[1] * is[1]), from_f2(i[2] * is[2], i[3] * is[3]));
+  }
+  static __device__ __forceinline__ V2 enc2(const float i[2], const float* is) {
+    return from_f2(i[0] * is[0], i[1] * is[1]);
+  }
 };
 
 template <>
-struct Codec<__half> {
+__device__ __forceinline__ float2 Codec16<__half, __half2>::to_f2(unsigned w) {
+  __half2 h;
+  memcpy(&h, &w, 4);
+  return __half22float2(h);
+}
+template <>
+__device__ __forceinline__ unsigned Codec16<__half, __half2>::from_f2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  unsigned w;
+  memcpy(&w, &h, 4);
+  return w;
+}
+template <>
+__device__ __forceinline__ float2 Codec16<__nv_bfloat16, __nv_bfloat162>::to_f2(unsigned w) {
+  __nv_bfloat162 h;
+  memcpy(&h, &w, 4);
+  return __bfloat1622float2(h);
+}
+template <>
+__device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162>::from_f2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  unsigned w;
+  memcpy(&w, &h, 4);
+  return w;
+}
+
+template <>
+struct Codec<__half> : Codec16<__half, __half2> {
   static __device__ __forceinline__ float dec(__half g, float s) { return __half2float(g) * s; }
   static __device__ __forceinline__ __half enc(float d, float inv_s) {
     return __float2half_rn(d * inv_s);
@@ -71,7 +141,7 @@ struct Codec<__half> {
 };
 
 template <>
-struct Codec<__nv_bfloat16> {
+struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16, __nv_bfloat162> {
   static __device__ __forceinline__ float dec(__nv_bfloat16 g, float s) {
     return __bfloat162float(g) * s;
   }
@@ -83,8 +153,37 @@ struct Codec<__nv_bfloat16> {
   }
 };
 
+// ---------------------------------------------------------------- layout
+// Tiled, direction-major layout. Cells are grouped in tiles of 32 consecutive cell
+// indices; a tile is one contiguous block of 98 x 32 elements holding, for each
+// storage slot (direction) s = 0..6, the 14 fields of its 32 cells as four field
+// groups: fields 0-3, 4-7, 8-11 as [lane][4] and fields 12-13 as [lane][2]. So a
+// thread moves the 14 fields of one direction with three 4-wide and one 2-wide
+// access (128/64-bit for FP32 storage), a warp's access covers contiguous bytes,
+// and every address is a per-cell base plus a compile-time offset.
+constexpr int kTile = 32;
+constexpr int kSlotElems = kF * kTile;   // 448 elements per slot per tile
+constexpr int kTileElems = kP * kTile;   // 3136 elements per tile
+
+// Element offset of field group g (0..2: fields 4g..4g+3; 3: fields 12, 13) of slot s
+// of lane `lane`, relative to the tile start.
+__host__ __device__ constexpr int group_offset(int s, int g, int lane) {
+  return s * kSlotElems + (g < 3 ? g * 4 * kTile + lane * 4 : 12 * kTile + lane * 2);
+}
+
+__host__ __device__ __forceinline__ long long tile_start(long long cell) {
+  return (cell >> 5) * (long long)kTileElems;
+}
+
+__host__ __device__ __forceinline__ long long pop_index(long long cell, int k, int slot) {
+  const int lane = (int)(cell & (kTile - 1));
+  const int g = k < 12 ? k >> 2 : 3;
+  const int j = k < 12 ? (k & 3) : k - 12;
+  return tile_start(cell) + group_offset(slot, g, lane) + j;
+}
+
 // ---------------------------------------------------------------- AA index maps
-// The state is one buffer pop[k][slot][cell]. After an even number of steps slot
+// The state is one buffer of populations (k, slot, cell). After an even number of steps slot
 // i of cell x holds f_i(x) (canonical). An even step reads its own slots and
 // writes f*_i into slot opp(i) of the same cell; an odd step reads f_i(x) from
 // slot opp(i) of cell x - e_i and writes f*_i into slot i of cell x + e_i. Every
@@ -116,15 +215,7 @@ __device__ __forceinline__ long long read_pos(const DomainConst& P, const CellIn
                                               int k, int i) {
   const long long cell = parity ? c.nb[opp(i)] : c.own;
   const int slot = parity ? opp(i) : i;
-  return (long long)(k * kQ + slot) * P.stride + cell;
-}
-
-// Cell and slot into which post-collision direction i of this cell is written.
-__device__ __forceinline__ long long write_pos(const DomainConst& P, const CellIndex& c,
-                                               int parity, int k, int i) {
-  const long long cell = parity ? c.nb[i] : c.own;
-  const int slot = parity ? i : opp(i);
-  return (long long)(k * kQ + slot) * P.stride + cell;
+  return pop_index(cell, k, slot);
 }
 
 // Held x ends: the inward population of a boundary cell comes from the ghost
@@ -140,27 +231,77 @@ __device__ __forceinline__ float ghost_value(const DomainConst& P, const float* 
   return ghost[((long long)side * kF + k) * planes + c.plane];
 }
 
+// Loads the 98 decoded deviations of this cell for a step of the given parity:
+// per direction i the source cell and slot of the AA map, then 4 + 4 + 4 + 2 fields.
 template <int PARITY, bool HELD, typename S>
 __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restrict__ pop,
                                           const float* __restrict__ ghost, const CellIndex& c,
                                           float (&d)[kF][kQ]) {
+  using V4 = typename Codec<S>::V4;
+  using V2 = typename Codec<S>::V2;
 #pragma unroll
-  for (int k = 0; k < kF; ++k) {
+  for (int i = 0; i < kQ; ++i) {
+    const long long cell = PARITY ? c.nb[opp(i)] : c.own;
+    const int slot = PARITY ? opp(i) : i;
+    const S* base = pop + tile_start(cell);
+    const int lane = (int)(cell & (kTile - 1));
+    float v[kF];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const S g = pop[read_pos(P, c, PARITY, k, i)];
-      d[k][i] = Codec<S>::dec(g, P.scale[k]);
-      if (HELD && (i == 1 || i == 2) && from_ghost(P, c, i)) d[k][i] = ghost_value(P, ghost, c, k, i);
+    for (int g = 0; g < 3; ++g) {
+      const V4 w = *reinterpret_cast<const V4*>(base + group_offset(slot, g, lane));
+      Codec<S>::dec4(w, P.scale + 4 * g, v + 4 * g);
+    }
+    const V2 w2 = *reinterpret_cast<const V2*>(base + group_offset(slot, 3, lane));
+    Codec<S>::dec2(w2, P.scale + 12, v + 12);
+#pragma unroll
+    for (int k = 0; k < kF; ++k) d[k][i] = v[k];
+    if (HELD && (i == 1 || i == 2) && from_ghost(P, c, i)) {
+#pragma unroll
+      for (int k = 0; k < kF; ++k) d[k][i] = ghost_value(P, ghost, c, k, i);
     }
   }
 }
 
+// Stores the 98 post-collision deviations: direction i goes to the slot and cell of
+// the AA map (own cell, slot opp(i) on even steps; cell x + e_i, slot i on odd steps).
 template <int PARITY, typename S>
-__device__ __forceinline__ void store_field(const DomainConst& P, S* __restrict__ pop,
-                                            const CellIndex& c, int k, const float (&dk)[kQ]) {
+__device__ __forceinline__ void store_cell(const DomainConst& P, S* __restrict__ pop,
+                                           const CellIndex& c, const float (&d)[kF][kQ]) {
+  using V4 = typename Codec<S>::V4;
+  using V2 = typename Codec<S>::V2;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) pop[write_pos(P, c, PARITY, k, i)] = Codec<S>::enc(dk[i], P.inv_scale[k]);
+  for (int i = 0; i < kQ; ++i) {
+    const long long cell = PARITY ? c.nb[i] : c.own;
+    const int slot = PARITY ? i : opp(i);
+    S* base = pop + tile_start(cell);
+    const int lane = (int)(cell & (kTile - 1));
+    float v[kF];
+#pragma unroll
+    for (int k = 0; k < kF; ++k) v[k] = d[k][i];
+#pragma unroll
+    for (int g = 0; g < 3; ++g)
+      *reinterpret_cast<V4*>(base + group_offset(slot, g, lane)) = Codec<S>::enc4(v + 4 * g, P.inv_scale + 4 * g);
+    *reinterpret_cast<V2*>(base + group_offset(slot, 3, lane)) = Codec<S>::enc2(v + 12, P.inv_scale + 12);
+  }
 }
+
+// ---------------------------------------------------------------- rounding-exact arithmetic
+// Every product, sum and fused multiply-add of the cell update is spelled out, so
+// the compiler cannot contract or reorder them differently in different kernels:
+// the single-domain kernels (both register budgets) and the batched kernel give
+// bit-identical populations.
+template <typename R> __device__ __forceinline__ R mul(R a, R b);
+template <typename R> __device__ __forceinline__ R add(R a, R b);
+template <typename R> __device__ __forceinline__ R sub(R a, R b);
+template <typename R> __device__ __forceinline__ R fma_(R a, R b, R c);
+template <> __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+template <> __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+template <> __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // ---------------------------------------------------------------- closure and flux
 // Primitive state of one cell in precision R (float in the step, double in the
@@ -175,10 +316,11 @@ struct Prim {
   R q[3];
 };
 
+// Sutherland factor mu_T / mu = (1 + T_S) t^{3/2} / (t + T_S), t = T / T_ref.
 template <typename R>
 __device__ __forceinline__ R sutherland_ratio(R T, R inv_T_ref) {
-  const R t = T * inv_T_ref;
-  return (R)(1.0 + 0.4042) * t * sqrt(t) / (t + (R)0.4042);
+  const R t = mul(T, inv_T_ref);
+  return mul(mul((R)(1.0 + 0.4042), t), (R)sqrt(t)) / add(t, (R)0.4042);
 }
 
 // Sec. 2.1: u = (rho u)/rho, p = (gamma-1)(E - rho|u|^2/2), T = p/rho; Sutherland.
@@ -190,16 +332,16 @@ __device__ __forceinline__ void closure(const R Q[kF], R gm1, R mu, R visc0, R h
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     s.m[a] = Q[1 + a];
-    s.u[a] = s.m[a] * s.inv_rho;
+    s.u[a] = mul(s.m[a], s.inv_rho);
   }
   s.E = Q[4];
-  const R ke = (R)0.5 * (s.m[0] * s.u[0] + s.m[1] * s.u[1] + s.m[2] * s.u[2]);
-  s.p = gm1 * (s.E - ke);
-  s.T = s.p * s.inv_rho;
+  const R ke = mul((R)0.5, fma_(s.m[2], s.u[2], fma_(s.m[1], s.u[1], mul(s.m[0], s.u[0]))));
+  s.p = mul(gm1, sub(s.E, ke));
+  s.T = mul(s.p, s.inv_rho);
   const R r = sutherland ? sutherland_ratio<R>(s.T, inv_T_ref) : (R)1;
-  s.mu_T = mu * r;
-  s.visc = visc0 * r;
-  s.heat = heat0 * r;
+  s.mu_T = mul(mu, r);
+  s.visc = mul(visc0, r);
+  s.heat = mul(heat0, r);
 #pragma unroll
   for (int j = 0; j < 6; ++j) s.tau[j] = Q[5 + j];
 #pragma unroll
@@ -213,28 +355,35 @@ __device__ __forceinline__ void field_flux(int k, const Prim<R>& s, R& fx, R& fy
   const R ux = s.u[0], uy = s.u[1], uz = s.u[2];
   const R txx = s.tau[0], tyy = s.tau[1], tzz = s.tau[2];
   const R txy = s.tau[3], txz = s.tau[4], tyz = s.tau[5];
-  const R v = s.visc, two3 = (R)(2.0 / 3.0), four3 = (R)(4.0 / 3.0);
+  const R v = s.visc;
+  const R v23 = mul(v, (R)(2.0 / 3.0)), v43 = mul(v, (R)(4.0 / 3.0));
   switch (k) {
     case 0: fx = s.m[0]; fy = s.m[1]; fz = s.m[2]; break;
-    case 1: fx = s.m[0] * ux + s.p - txx; fy = s.m[0] * uy - txy; fz = s.m[0] * uz - txz; break;
-    case 2: fx = s.m[1] * ux - txy; fy = s.m[1] * uy + s.p - tyy; fz = s.m[1] * uz - tyz; break;
-    case 3: fx = s.m[2] * ux - txz; fy = s.m[2] * uy - tyz; fz = s.m[2] * uz + s.p - tzz; break;
+    case 1:
+      fx = sub(fma_(s.m[0], ux, s.p), txx); fy = sub(mul(s.m[0], uy), txy); fz = sub(mul(s.m[0], uz), txz);
+      break;
+    case 2:
+      fx = sub(mul(s.m[1], ux), txy); fy = sub(fma_(s.m[1], uy, s.p), tyy); fz = sub(mul(s.m[1], uz), tyz);
+      break;
+    case 3:
+      fx = sub(mul(s.m[2], ux), txz); fy = sub(mul(s.m[2], uy), tyz); fz = sub(fma_(s.m[2], uz, s.p), tzz);
+      break;
     case 4: {
-      const R h = s.E + s.p;
-      fx = h * ux - (txx * ux + txy * uy + txz * uz) + s.q[0];
-      fy = h * uy - (txy * ux + tyy * uy + tyz * uz) + s.q[1];
-      fz = h * uz - (txz * ux + tyz * uy + tzz * uz) + s.q[2];
+      const R h = add(s.E, s.p);
+      fx = add(sub(mul(h, ux), fma_(txz, uz, fma_(txy, uy, mul(txx, ux)))), s.q[0]);
+      fy = add(sub(mul(h, uy), fma_(tyz, uz, fma_(tyy, uy, mul(txy, ux)))), s.q[1]);
+      fz = add(sub(mul(h, uz), fma_(tzz, uz, fma_(tyz, uy, mul(txz, ux)))), s.q[2]);
       break;
     }
-    case 5: fx = txx * ux - v * four3 * ux; fy = txx * uy + v * two3 * uy; fz = txx * uz + v * two3 * uz; break;
-    case 6: fx = tyy * ux + v * two3 * ux; fy = tyy * uy - v * four3 * uy; fz = tyy * uz + v * two3 * uz; break;
-    case 7: fx = tzz * ux + v * two3 * ux; fy = tzz * uy + v * two3 * uy; fz = tzz * uz - v * four3 * uz; break;
-    case 8: fx = txy * ux - v * uy; fy = txy * uy - v * ux; fz = txy * uz; break;
-    case 9: fx = txz * ux - v * uz; fy = txz * uy; fz = txz * uz - v * ux; break;
-    case 10: fx = tyz * ux; fy = tyz * uy - v * uz; fz = tyz * uz - v * uy; break;
-    case 11: fx = s.q[0] * ux + s.heat * s.T; fy = s.q[0] * uy; fz = s.q[0] * uz; break;
-    case 12: fx = s.q[1] * ux; fy = s.q[1] * uy + s.heat * s.T; fz = s.q[1] * uz; break;
-    default: fx = s.q[2] * ux; fy = s.q[2] * uy; fz = s.q[2] * uz + s.heat * s.T; break;
+    case 5: fx = sub(mul(txx, ux), mul(v43, ux)); fy = fma_(v23, uy, mul(txx, uy)); fz = fma_(v23, uz, mul(txx, uz)); break;
+    case 6: fx = fma_(v23, ux, mul(tyy, ux)); fy = sub(mul(tyy, uy), mul(v43, uy)); fz = fma_(v23, uz, mul(tyy, uz)); break;
+    case 7: fx = fma_(v23, ux, mul(tzz, ux)); fy = fma_(v23, uy, mul(tzz, uy)); fz = sub(mul(tzz, uz), mul(v43, uz)); break;
+    case 8: fx = sub(mul(txy, ux), mul(v, uy)); fy = sub(mul(txy, uy), mul(v, ux)); fz = mul(txy, uz); break;
+    case 9: fx = sub(mul(txz, ux), mul(v, uz)); fy = mul(txz, uy); fz = sub(mul(txz, uz), mul(v, ux)); break;
+    case 10: fx = mul(tyz, ux); fy = sub(mul(tyz, uy), mul(v, uz)); fz = sub(mul(tyz, uz), mul(v, uy)); break;
+    case 11: fx = fma_(s.q[0], ux, mul(s.heat, s.T)); fy = mul(s.q[0], uy); fz = mul(s.q[0], uz); break;
+    case 12: fx = mul(s.q[1], ux); fy = fma_(s.q[1], uy, mul(s.heat, s.T)); fz = mul(s.q[1], uz); break;
+    default: fx = mul(s.q[2], ux); fy = mul(s.q[2], uy); fz = fma_(s.q[2], uz, mul(s.heat, s.T)); break;
   }
 }
 
@@ -257,19 +406,19 @@ __device__ __forceinline__ float collide_cell(const DomainConst& P, float (&d)[k
   for (int k = 0; k < kF; ++k) {
     float s = d[k][0];
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) s += d[k][i];
+    for (int i = 1; i < kQ; ++i) s = add(s, d[k][i]);
     D[k] = s;
   }
   float Q[kF];
 #pragma unroll
   for (int k = 0; k < kF; ++k) Q[k] = D[k];
-  Q[0] += P.rho_ref;
-  Q[4] += P.E_ref;
+  Q[0] = add(Q[0], P.rho_ref);
+  Q[4] = add(Q[4], P.E_ref);
   Prim<float> s;
   closure<float>(Q, P.gm1, P.mu, P.visc0, P.heat0, P.inv_T_ref, P.sutherland, s);
 
   // Eq. 6: tau_base = 1/2 + 4 f_mu (mu_T/rho) dt/dx^2, omega = 1/tau_base.
-  const float tau_b = 0.5f + P.fmu_coef * s.mu_T * s.inv_rho;
+  const float tau_b = fma_(mul(P.fmu_coef, s.mu_T), s.inv_rho, 0.5f);
   const float omega = 1.0f / tau_b;
 
   // Local dilatation from the cell's own non-equilibrium moments (pre-collision):
@@ -279,51 +428,51 @@ __device__ __forceinline__ float collide_cell(const DomainConst& P, float (&d)[k
   // so, in lattice units (theta dt) with tau = tau_base:
   //   theta dt = 4 omega / rho [fneq_{rho,0} - sum_a (u_a/c)(4 fneq_{rho u_a,0}/c
   //                                                   - (d_{rho,+a} - d_{rho,-a}) + m_a/c)].
-  float acc = d[0][0] - 0.25f * D[0];
+  float acc = sub(d[0][0], mul(0.25f, D[0]));
   if (P.sensor_mode == 0) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float fneq_m0 = d[1 + a][0] - 0.25f * D[1 + a];
-      const float g = 4.0f * fneq_m0 * P.inv_c - (d[0][2 * a + 1] - d[0][2 * a + 2]) + s.m[a] * P.inv_c;
-      acc -= s.u[a] * P.inv_c * g;
+      const float fneq_m0 = sub(d[1 + a][0], mul(0.25f, D[1 + a]));
+      const float g = fma_(s.m[a], P.inv_c, sub(mul(mul(4.0f, fneq_m0), P.inv_c),
+                                                  sub(d[0][2 * a + 1], d[0][2 * a + 2])));
+      acc = sub(acc, mul(mul(s.u[a], P.inv_c), g));
     }
   }
-  const float theta_dt = 4.0f * omega * s.inv_rho * acc;
+  const float theta_dt = mul(mul(mul(4.0f, omega), s.inv_rho), acc);
   // Eq. 3: s = max(0, -div u)/c_s with c_s = 1/2 in lattice units.
-  const float smach = 2.0f * fmaxf(0.0f, -theta_dt);
+  const float smach = mul(2.0f, fmaxf(0.0f, -theta_dt));
   // Eq. 4 and Eq. 5.
-  const float chi = (smach > P.J_min) ? fminf(P.C_sigma * smach, 1.0f) : 0.0f;
-  const float om = omega - chi * (omega - P.omega_min);
+  const float chi = (smach > P.J_min) ? fminf(mul(P.C_sigma, smach), 1.0f) : 0.0f;
+  const float om = sub(omega, mul(chi, sub(omega, P.omega_min)));
   if constexpr (kSensor) {
     so->theta_dt = theta_dt;
     so->chi = chi;
     so->omega_h = om;
     return D[0];
   } else {
-
-  // Collision, field by field: d* = d + omega_h (deq - d) + w_i dS_k with
-  // deq_0 = D/4, deq_{+-a} = D/8 +- Phi_a / (2c).
+    // Collision, field by field: d* = d + omega_h (deq - d) + w_i dS_k with
+    // deq_0 = D/4, deq_{+-a} = D/8 +- Phi_a / (2c).
 #pragma unroll
-  for (int k = 0; k < kF; ++k) {
-    float fx, fy, fz;
-    field_flux<float>(k, s, fx, fy, fz);
-    const float e0 = 0.25f * D[k], e1 = 0.125f * D[k];
-    const float ax = P.half_inv_c * fx, ay = P.half_inv_c * fy, az = P.half_inv_c * fz;
-    float dS = 0.0f;
-    if (k >= 5) dS = (k < 11 ? P.src_R : P.src_q) * D[k];
-    const float s0 = 0.25f * dS, s1 = 0.125f * dS;
-    d[k][0] = fmaf(om, e0 - d[k][0], d[k][0]) + s0;
-    d[k][1] = fmaf(om, (e1 + ax) - d[k][1], d[k][1]) + s1;
-    d[k][2] = fmaf(om, (e1 - ax) - d[k][2], d[k][2]) + s1;
-    d[k][3] = fmaf(om, (e1 + ay) - d[k][3], d[k][3]) + s1;
-    d[k][4] = fmaf(om, (e1 - ay) - d[k][4], d[k][4]) + s1;
-    d[k][5] = fmaf(om, (e1 + az) - d[k][5], d[k][5]) + s1;
-    d[k][6] = fmaf(om, (e1 - az) - d[k][6], d[k][6]) + s1;
-  }
-  float probe = 0.0f;
+    for (int k = 0; k < kF; ++k) {
+      float fx, fy, fz;
+      field_flux<float>(k, s, fx, fy, fz);
+      const float e0 = mul(0.25f, D[k]), e1 = mul(0.125f, D[k]);
+      const float ax = mul(P.half_inv_c, fx), ay = mul(P.half_inv_c, fy), az = mul(P.half_inv_c, fz);
+      float dS = 0.0f;
+      if (k >= 5) dS = mul(k < 11 ? P.src_R : P.src_q, D[k]);
+      const float s0 = mul(0.25f, dS), s1 = mul(0.125f, dS);
+      d[k][0] = add(fma_(om, sub(e0, d[k][0]), d[k][0]), s0);
+      d[k][1] = add(fma_(om, sub(add(e1, ax), d[k][1]), d[k][1]), s1);
+      d[k][2] = add(fma_(om, sub(sub(e1, ax), d[k][2]), d[k][2]), s1);
+      d[k][3] = add(fma_(om, sub(add(e1, ay), d[k][3]), d[k][3]), s1);
+      d[k][4] = add(fma_(om, sub(sub(e1, ay), d[k][4]), d[k][4]), s1);
+      d[k][5] = add(fma_(om, sub(add(e1, az), d[k][5]), d[k][5]), s1);
+      d[k][6] = add(fma_(om, sub(sub(e1, az), d[k][6]), d[k][6]), s1);
+    }
+    float probe = 0.0f;
 #pragma unroll
-  for (int k = 0; k < kF; ++k) probe += D[k];
-  return probe;
+    for (int k = 0; k < kF; ++k) probe = add(probe, D[k]);
+    return probe;
   }
 }
 

@@ -7,13 +7,14 @@
 
 namespace lbm {
 
-// Fused step: one launch per time step, grid (ceil(nx/block_x), ny, nz).
+// Fused step: one launch per time step, grid (ceil(nx/block_x), ny, nz), block_x in
+// {32, 64, 96, 128}; variant selects the register budget (0: 170, 1: 128 registers).
 cudaError_t launch_step_f32(const DomainConst& P, int parity, void* pop, const float* ghost,
-                            unsigned* flag, int block_x, cudaStream_t s);
+                            unsigned* flag, int block_x, int variant, cudaStream_t s);
 cudaError_t launch_step_f16(const DomainConst& P, int parity, void* pop, const float* ghost,
-                            unsigned* flag, int block_x, cudaStream_t s);
+                            unsigned* flag, int block_x, int variant, cudaStream_t s);
 cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const float* ghost,
-                             unsigned* flag, int block_x, cudaStream_t s);
+                             unsigned* flag, int block_x, int variant, cudaStream_t s);
 
 // Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields.
 struct InitSpec {

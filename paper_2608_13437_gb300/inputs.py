@@ -31,10 +31,12 @@ _F_MU_LISTED = {64: 1.8, 128: 0.9, 192: 3e-2, 256: 1e-2, 320: 8e-3, 384: 1e-2, 5
 
 
 def tgv_f_mu(n: int) -> float:
+    """Listed sizes take their value; sizes below 64 take the 64^3 value and the
+    others that of the next listed size up (96 -> 0.9)."""
     if n in _F_MU_LISTED:
         return _F_MU_LISTED[n]
-    coarser = [k for k in sorted(_F_MU_LISTED) if k <= n]
-    return _F_MU_LISTED[coarser[-1]] if coarser else _F_MU_LISTED[64]
+    finer = [k for k in sorted(_F_MU_LISTED) if k >= n]
+    return _F_MU_LISTED[finer[0]] if finer else _F_MU_LISTED[max(_F_MU_LISTED)]
 
 
 def tgv_params(n: int, M0: float = 1.25, Re: float = 1000.0, Pr: float = 0.71,
@@ -117,18 +119,33 @@ class SplitMix64:
 
 
 BATCH_SIZES = (32, 48, 64, 96, 128)
+# The TGV initial pressure p0 + rho0 U0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2) has its
+# minimum p0 - 3 rho0 U0^2 / 8 at grid nodes (x = y = pi/2, z = 0). With
+# p0 = rho0 U0^2 / (gamma M0^2) and uniform T0 the minimum density is
+# rho0 (1 - 3 gamma M0^2 / 8): negative for M0 > sqrt(8 / (3 gamma)) = 1.380, and a
+# near-vacuum below it. Draws must keep it at or above 5 % of rho0.
+TGV_RHO_MIN_FRACTION = 0.05
+TGV_M0_ADMISSIBLE = math.sqrt((1.0 - TGV_RHO_MIN_FRACTION) * 8.0 / (3.0 * GAMMA))
 
 
-def batch_domains(n_domains: int = 64, seed: int = 0, sizes=BATCH_SIZES) -> list[dict]:
+def batch_domains(n_domains: int = 64, seed: int = 0, sizes=BATCH_SIZES,
+                  m0_range=(0.3, 1.5), re_range=(100.0, 1600.0)) -> list[dict]:
     """Independent periodic TGV domains: per domain, in order, a size index uniform
-    in `sizes`, then M0 ~ U[0.3, 1.5], then Re ~ U[100, 1600]."""
+    in `sizes`, then M0 ~ U[0.3, 1.5], then Re ~ U[100, 1600]. An M0 draw whose
+    initial state has (near-)vacuum regions (M0 >= TGV_M0_ADMISSIBLE) is rejected and
+    drawn again from the same stream, so M0 is uniform on the admissible part."""
     rng = SplitMix64(seed)
     out = []
     for d in range(n_domains):
         n = sizes[min(int(rng.uniform() * len(sizes)), len(sizes) - 1)]
-        M0 = 0.3 + 1.2 * rng.uniform()
-        Re = 100.0 + 1500.0 * rng.uniform()
-        out.append(dict(index=d, n=n, M0=M0, Re=Re))
+        redraws = 0
+        while True:
+            M0 = m0_range[0] + (m0_range[1] - m0_range[0]) * rng.uniform()
+            if M0 < TGV_M0_ADMISSIBLE:
+                break
+            redraws += 1
+        Re = re_range[0] + (re_range[1] - re_range[0]) * rng.uniform()
+        out.append(dict(index=d, n=n, M0=M0, Re=Re, redraws=redraws))
     return out
 
 
@@ -166,3 +183,26 @@ def random_smooth_state(nx: int, ny: int, nz: int, seed: int, amp: float = 0.1,
     p = 1.0 + amp * field()
     u = [amp * field() for _ in range(3)]
     return dict(rho=rho, ux=u[0], uy=u[1], uz=u[2], p=p)
+
+
+def tgv_fields(n: int, M0: float = 1.25, U0: float = 1.0, rho0: float = 1.0,
+               dtype=np.float32) -> np.ndarray:
+    """The TGV initial fields of Sec. 3.2 on the n^3 nodes (i, j, l) * 2 pi / n, as one
+    (5, n, n, n) array [z][y][x] of rho, u_x, u_y, u_z, p (input data for callers that
+    supply their own initial state)."""
+    h = 2.0 * math.pi / n
+    x = np.arange(n) * h
+    sx, cx, c2x = np.sin(x), np.cos(x), np.cos(2 * x)
+    p0 = rho0 * U0 * U0 / (GAMMA * M0 * M0)
+    T0 = p0 / rho0
+    out = np.empty((5, n, n, n), dtype=dtype)
+    for z in range(n):
+        cz = math.cos(z * h)
+        c2z = math.cos(2 * z * h)
+        out[1, z] = U0 * sx[None, :] * cx[:, None] * cz
+        out[2, z] = -U0 * cx[None, :] * sx[:, None] * cz
+        out[3, z] = 0.0
+        p = p0 + rho0 * U0 * U0 / 16.0 * (c2x[None, :] + c2x[:, None]) * (c2z + 2.0)
+        out[4, z] = p
+        out[0, z] = p / T0
+    return out

@@ -42,6 +42,7 @@ class LbmInfo(ctypes.Structure):
         ("tau_q", ctypes.c_double), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
         ("scale", ctypes.c_double * 14), ("step", ctypes.c_longlong), ("ncell", ctypes.c_longlong),
         ("population_bytes", ctypes.c_size_t), ("store", ctypes.c_int), ("block_x", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -54,7 +55,7 @@ class LbmDiag(ctypes.Structure):
 
 
 class LbmTune(ctypes.Structure):
-    _fields_ = [("block_x", ctypes.c_int), ("ms_per_step", ctypes.c_float),
+    _fields_ = [("block_x", ctypes.c_int), ("variant", ctypes.c_int), ("ms_per_step", ctypes.c_float),
                 ("candidates", ctypes.c_int)]
 
 
@@ -91,6 +92,7 @@ _SIGNATURES = {
     "lbm_save": (_IP, [_VP, ctypes.c_char_p]),
     "lbm_load": (_IP, [_VP, ctypes.c_char_p]),
     "lbm_autotune": (_IP, [_VP, _IP, ctypes.POINTER(LbmTune)]),
+    "lbm_set_kernel_config": (_IP, [_VP, _IP, _IP]),
     "lbm_batch_create": (_IP, [_IP, ctypes.POINTER(LbmParams), ctypes.POINTER(_VP)]),
     "lbm_batch_destroy": (_IP, [_VP]),
     "lbm_batch_init_tgv": (_IP, [_VP, _DP, _DP, _DP]),
@@ -151,6 +153,8 @@ class Domain:
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
         self.stream = torch.cuda.current_stream(self.device)
         self.params = dict(params)
@@ -291,10 +295,14 @@ class Domain:
     def load(self, path: str):
         check(lib().lbm_load(self._h, path.encode()))
 
+    def set_kernel_config(self, block_x: int, variant: int):
+        check(lib().lbm_set_kernel_config(self._h, int(block_x), int(variant)))
+
     def autotune(self, pairs_per_trial=4) -> dict:
         t = LbmTune()
         check(lib().lbm_autotune(self._h, int(pairs_per_trial), ctypes.byref(t)))
-        return {"block_x": t.block_x, "ms_per_step": t.ms_per_step, "candidates": t.candidates}
+        return {"block_x": t.block_x, "variant": t.variant, "ms_per_step": t.ms_per_step,
+                "candidates": t.candidates}
 
 
 class Batch:
@@ -304,6 +312,8 @@ class Batch:
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
         self.stream = torch.cuda.current_stream(self.device)
         arr = (LbmParams * len(param_list))(*[make_params(p, "f32", stream=self.stream.cuda_stream)

@@ -35,11 +35,13 @@ def test_population_bytes_layout(L):
     assert L.lbm_population_bytes(ctypes.byref(p)) == 98 * 32 ** 3 * 4
     p = lbm.make_params(inputs.tgv_params(32), "f16")
     assert L.lbm_population_bytes(ctypes.byref(p)) == 98 * 32 ** 3 * 2
-    # each array padded to 256 bytes
+    # whole tiles of 32 cells
     q = dict(inputs.tgv_params(8))
     q.update(nx=5, ny=3, nz=1)
     p = lbm.make_params(q, "f32")
-    assert L.lbm_population_bytes(ctypes.byref(p)) == 98 * 256
+    assert L.lbm_population_bytes(ctypes.byref(p)) == 98 * 32 * 4
+    q.update(nx=33)
+    assert L.lbm_population_bytes(ctypes.byref(lbm.make_params(q, "bf16"))) == 4 * 98 * 32 * 2
     q.update(nx=0)
     assert L.lbm_population_bytes(ctypes.byref(lbm.make_params(q, "f32"))) == 0
 
