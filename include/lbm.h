@@ -225,6 +225,19 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype);
  * found (returned by this call as well, after *out is filled). */
 lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out);
 
+/* lbm_diag without any memory allocation (no counterpart in the paper; a service
+ * for callers that cannot allocate device memory when they sample diagnostics,
+ * for example because a memory pool already holds the free device memory or
+ * because cudaMalloc's device-wide synchronisation is not acceptable there).
+ * Same results as lbm_diag. Its scratch is a fixed device array inside the
+ * library (about 8.3 MiB on every device that loads the library, kept until the
+ * process exits), so it handles domains of at most 262144 cells (64^3) and returns
+ * LBM_E_INVAL for larger ones. The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture. Calls share the array: two calls whose kernels overlap on the
+ * GPU race, so serialise them. Synchronises the handle's stream. */
+lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out);
+
 /* Canonical populations [k][i][z][y][x] in `dtype`: F64/F32 = the physical f
  * (decoded), NATIVE = the stored bits. */
 lbm_status lbm_populations_get(lbm_handle* h, void* dst, int dst_on_device, int dtype);

@@ -829,3 +829,29 @@ lbm_status lbm_load(lbm_handle* h, const char* path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- internal view
+// Read access to a handle's device state for other translation units of the
+// library (the fixed-scratch diagnostics in diag_static.cu), plus the one latch
+// they may set.
+namespace lbm {
+
+HandleView handle_view(lbm_handle* h) {
+  HandleView v;
+  v.P = &h->P;
+  v.store = h->prm.store;
+  v.step = h->step;
+  v.dt = h->dt;
+  v.pop = h->pop;
+  v.ghost = h->ghost;
+  v.flag = h->flag;
+  v.stream = h->stream;
+  v.ncell = h->ncell;
+  return v;
+}
+
+void latch_nonfinite(lbm_handle* h) { h->nonfinite = true; }
+
+bool nonfinite_latched(const lbm_handle* h) { return h->nonfinite; }
+
+}  // namespace lbm

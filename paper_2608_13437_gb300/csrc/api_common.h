@@ -19,4 +19,20 @@ cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, 
                         unsigned* flag, int block_x, int variant, cudaStream_t s);
 bool finite_pos(double v);
 
+// Device state of a handle, for library code outside api.cu.
+struct HandleView {
+  const DomainConst* P;
+  int store;
+  long long step;
+  double dt;
+  const void* pop;
+  const float* ghost;
+  unsigned* flag;
+  cudaStream_t stream;
+  long long ncell;
+};
+HandleView handle_view(lbm_handle* h);
+void latch_nonfinite(lbm_handle* h);
+bool nonfinite_latched(const lbm_handle* h);
+
 }  // namespace lbm

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "lbm_moments": (_IP, [_VP, _IP, _VP, _IP, _IP]),
     "lbm_sensor": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_diag": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
+    "lbm_diag_static": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
     "lbm_populations_get": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_populations_set": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_save": (_IP, [_VP, ctypes.c_char_p]),
