@@ -134,6 +134,21 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def reduce_max(x, dist, device):
+    """Maximum of a per-rank number over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ncell, steps, ms_max):
+    """Whole-job MLUPS: all ranks' cell updates over the slowest rank's time."""
+    return world * ncell * steps / (ms_max * 1e-3) / 1e6
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -252,10 +267,11 @@ def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
     return ms, clocks
 
 
-def batch_leg(torch, lbm, inputs, steps, warmup):
-    """64 independent TGV domains (sizes, M0, Re from SplitMix64(0)): one persistent
-    launch per step (CUDA graph, autotuned tiles) against 64 plain launches per step."""
-    doms = inputs.batch_domains()
+def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64):
+    """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
+    persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
+    per domain per step."""
+    doms = inputs.batch_domains()[:n_domains]
     pl = inputs.batch_params(doms)
     B = lbm.Batch([q for q, _ in pl])
     ic = [[c["U0"] for _, c in pl], [c["M0"] for _, c in pl], [c["rho0"] for _, c in pl]]
@@ -307,13 +323,9 @@ def run_gpu(args):
     dom.init_tgv(1.0, 1.25, 1.0)
     ms_total, clocks = time_steps(torch, dom, args.steps, args.warmup, dist,
                                   sampler_index=dev if rank == 0 else None)
-    ms_max = ms_total
-    if dist:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_max / args.steps
-    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+    value = job_value(world, ncell, args.steps, ms_max)
     hbm, peak_kind = peaks()
     bpc = BYTES_PER_CELL[args.store]
     achieved = bpc * ncell / (ms_total / args.steps * 1e-3) / 1e9
@@ -342,12 +354,8 @@ def run_gpu(args):
             series.append(dom.diag())
     dom.moments_into(out, which=lbm.MOM_PRIM, on_device=False)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": round(world * ncell * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": round(job_value(world, ncell, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(fields.numel() * 4 / args.steps),
            "d2h_bytes_per_step": int((out.numel() * 4 + len(series) * 15 * 8) / args.steps),
            "api": "lbm_init_fields(host) + lbm_step + lbm_diag every 50 steps + lbm_moments(host)",
@@ -409,6 +417,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage legs")
+    ap.add_argument("--only-batch", type=int, default=0, metavar="K",
+                    help="run only the batched-mode leg on the first K seeded domains")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -417,6 +427,14 @@ def main():
         return
     from paper_2608_13437_gb300 import build
     build.build()
+    if args.only_batch:
+        import torch
+
+        from paper_2608_13437_gb300 import inputs, lbm
+        torch.cuda.set_device(0)
+        print(json.dumps(batch_leg(torch, lbm, inputs, args.steps, args.warmup, args.only_batch)),
+              flush=True)
+        return
     run_gpu(args)
 
 

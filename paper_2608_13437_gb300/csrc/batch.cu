@@ -1,9 +1,9 @@
 // Batched mode: many independent periodic domains of different sizes and
 // parameters, stored in one buffer, advanced by ONE persistent launch per time
 // step. The grid holds as many blocks as are resident on the GPU. Each block
-// stages every domain's constants in shared memory once; then each warp works on
-// its own items, an item being `tiles_per_item` consecutive 32-cell layout tiles
-// (warp w takes items w, w + warps, ...). A tile's domain is found by binary search
+// stages every domain's constants in shared memory once; then each warp claims
+// items from a counter, an item being `tiles_per_item` consecutive 32-cell layout
+// tiles, until none are left. A tile's domain is found by binary search
 // in the per-domain tile prefix sums; no block-wide synchronisation happens after
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
 // update is the single-domain one. Items per warp, block size and register budget
@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
                                                           const int* __restrict__ tile_prefix,
                                                           int ndom, int total_tiles,
                                                           int tiles_per_item,
+                                                          unsigned* __restrict__ next_item,
                                                           unsigned* __restrict__ flag) {
   extern __shared__ __align__(16) unsigned char smem[];
   DomainConst* sP = reinterpret_cast<DomainConst*>(smem);
@@ -42,9 +43,15 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int item = warp; item * tiles_per_item < total_tiles; item += nwarps) {
+  const int n_items = (total_tiles + tiles_per_item - 1) / tiles_per_item;
+  // Items are claimed in order from one counter (zeroed before the launch), so the
+  // tiles in flight stay a compact window of the buffer, as with hardware block
+  // scheduling. The next claim is issued before the current item is processed.
+  unsigned claim = 0;
+  if (lane == 0) claim = atomicAdd(next_item, 1u);
+  int item = (int)__shfl_sync(0xffffffffu, claim, 0);
+  while (item < n_items) {
+    if (lane == 0) claim = atomicAdd(next_item, 1u);
     const int t_end = min(total_tiles, (item + 1) * tiles_per_item);
     for (int t = item * tiles_per_item; t < t_end; ++t) {
       int lo = 0, hi = ndom;  // sPrefix[lo] <= t < sPrefix[hi]
@@ -79,6 +86,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
       if (!isfinite(probe)) atomicOr(flag, 1u);
       store_cell<PARITY, float>(P, pop, c, d);
     }
+    item = (int)__shfl_sync(0xffffffffu, claim, 0);
   }
 }
 
@@ -96,6 +104,7 @@ struct lbm_batch {
   DomainConst* d_consts = nullptr;
   float** d_pops = nullptr;
   int* d_prefix = nullptr;     // per-domain prefix sums of 32-cell tiles (n + 1)
+  unsigned* d_counter = nullptr;  // work-item counter of the persistent kernel
   int total_tiles = 0;
   int tiles_per_item = 4;      // layout tiles a warp takes at a time
   int block = 64;
@@ -153,14 +162,17 @@ lbm_status size_grid(lbm_batch* b) {
   return LBM_OK;
 }
 
+// One persistent launch: zero the work-item counter, then the kernel.
 cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
   const dim3 g(b->grid), bl(b->block);
   if (b->variant) {
-    if (parity) k_batch_step<1, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
-    else k_batch_step<0, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+    if (parity) k_batch_step<1, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
   } else {
-    if (parity) k_batch_step<1, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
-    else k_batch_step<0, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->flag);
+    if (parity) k_batch_step<1, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
   }
   return cudaGetLastError();
 }
@@ -249,6 +261,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pops, sizeof(float*) * n) != cudaSuccess ||
       cudaMalloc(&b->d_prefix, sizeof(int) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, 64) != cudaSuccess ||
       cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
@@ -275,6 +288,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->d_consts) cudaFree(b->d_consts);
   if (b->d_pops) cudaFree(b->d_pops);
   if (b->d_prefix) cudaFree(b->d_prefix);
+  if (b->d_counter) cudaFree(b->d_counter);
   if (b->flag) cudaFree(b->flag);
   if (b->ghost) cudaFree(b->ghost);
   if (b->cap) cudaStreamDestroy(b->cap);

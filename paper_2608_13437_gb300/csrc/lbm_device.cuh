@@ -75,8 +75,9 @@ struct Codec<float> {
   }
 };
 
-// 16-bit codecs: pairs of values travel as one 32-bit word.
-template <typename H, typename H2>
+// 16-bit codecs: pairs of values travel as one 32-bit word. kScaled: FP16 applies the
+// per-field scale; BF16 has the exponent range of FP32 and stores unscaled (s = 1).
+template <typename H, typename H2, bool kScaled>
 struct Codec16 {
   using V4 = uint2;
   using V2 = unsigned;
@@ -84,8 +85,8 @@ struct Codec16 {
   static __device__ __forceinline__ unsigned from_f2(float a, float b);
   static __device__ __forceinline__ void dec2w(unsigned w, const float* s, float* o) {
     const float2 f = to_f2(w);
-    o[0] = f.x * s[0];
-    o[1] = f.y * s[1];
+    o[0] = kScaled ? f.x * s[0] : f.x;
+    o[1] = kScaled ? f.y * s[1] : f.y;
   }
   static __device__ __forceinline__ void dec4(const V4& v, const float* s, float o[4]) {
     dec2w(v.x, s, o);
@@ -95,34 +96,36 @@ struct Codec16 {
     dec2w(v, s, o);
   }
   static __device__ __forceinline__ V4 enc4(const float i[4], const float* is) {
+    if (!kScaled) return make_uint2(from_f2(i[0], i[1]), from_f2(i[2], i[3]));
     return make_uint2(from_f2(i[0] * is[0], i[1] * is[1]), from_f2(i[2] * is[2], i[3] * is[3]));
   }
   static __device__ __forceinline__ V2 enc2(const float i[2], const float* is) {
+    if (!kScaled) return from_f2(i[0], i[1]);
     return from_f2(i[0] * is[0], i[1] * is[1]);
   }
 };
 
 template <>
-__device__ __forceinline__ float2 Codec16<__half, __half2>::to_f2(unsigned w) {
+__device__ __forceinline__ float2 Codec16<__half, __half2, true>::to_f2(unsigned w) {
   __half2 h;
   memcpy(&h, &w, 4);
   return __half22float2(h);
 }
 template <>
-__device__ __forceinline__ unsigned Codec16<__half, __half2>::from_f2(float a, float b) {
+__device__ __forceinline__ unsigned Codec16<__half, __half2, true>::from_f2(float a, float b) {
   const __half2 h = __floats2half2_rn(a, b);
   unsigned w;
   memcpy(&w, &h, 4);
   return w;
 }
 template <>
-__device__ __forceinline__ float2 Codec16<__nv_bfloat16, __nv_bfloat162>::to_f2(unsigned w) {
+__device__ __forceinline__ float2 Codec16<__nv_bfloat16, __nv_bfloat162, false>::to_f2(unsigned w) {
   __nv_bfloat162 h;
   memcpy(&h, &w, 4);
   return __bfloat1622float2(h);
 }
 template <>
-__device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162>::from_f2(float a, float b) {
+__device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162, false>::from_f2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   unsigned w;
   memcpy(&w, &h, 4);
@@ -130,7 +133,7 @@ __device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162>::from
 }
 
 template <>
-struct Codec<__half> : Codec16<__half, __half2> {
+struct Codec<__half> : Codec16<__half, __half2, true> {
   static __device__ __forceinline__ float dec(__half g, float s) { return __half2float(g) * s; }
   static __device__ __forceinline__ __half enc(float d, float inv_s) {
     return __float2half_rn(d * inv_s);
@@ -141,7 +144,7 @@ struct Codec<__half> : Codec16<__half, __half2> {
 };
 
 template <>
-struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16, __nv_bfloat162> {
+struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16, __nv_bfloat162, false> {
   static __device__ __forceinline__ float dec(__nv_bfloat16 g, float s) {
     return __bfloat162float(g) * s;
   }

@@ -1,0 +1,127 @@
+"""Full-size and convergence checks on the GPU:
+  * 512^3 TGV in the benchmark's launch configuration against the oracle on a light
+    cone: after n steps a cell depends only on cells within n lattice steps, so the
+    oracle recomputes a (B + 2n)^3 window of the same initial field and its central
+    B^3 cells must match the GPU's (sampled outputs at full size);
+  * Sod at 256..2048 cells: shock position, first-order thickness, L1 falling;
+  * reduced storage at 128^3 against the FP64 oracle and the FP32 GPU path.
+"""
+import numpy as np
+import pytest
+
+from conftest import make_oracle
+from paper_2608_13437_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_13437_gb300 import build, lbm as L
+    build.build()
+    L.lib()
+    return L
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("steps", [40, 41])
+def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps):
+    import torch
+    n, B = 512, 12
+    origin = (100, 250, 400)
+    p = inputs.tgv_params(n)
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.autotune(pairs_per_trial=2)  # the benchmark's configuration; re-init after
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.step(steps)
+    dom.synchronize()
+    prim = dom.moments_device(lbm.MOM_PRIM, torch.float64)
+    x0, y0, z0 = origin
+    g = prim[:, z0:z0 + B, y0:y0 + B, x0:x0 + B].cpu().numpy()
+    del prim
+    dom.close()
+    torch.cuda.empty_cache()
+    side = B + 2 * steps
+    q = dict(p)
+    q.update(nx=side, ny=side, nz=side)
+    o = make_oracle(q)
+    o.init_tgv(1.0, 1.25, 1.0, gn=n, origin=(x0 - steps, y0 - steps, z0 - steps))
+    o.step(steps)
+    r = o.primitives()[:, steps:steps + B, steps:steps + B, steps:steps + B]
+    errs = {"rho": rel_l2(g[0], r[0]), "u": rel_l2(g[1:4], r[1:4]), "T": rel_l2(g[4], r[4])}
+    assert max(errs.values()) < 1e-5, errs
+
+
+def test_sod_convergence_gpu(lbm):
+    """Sec. 3.1, Tables 2 and 4: the captured shock thickness holds a fixed number of
+    cells (w proportional to dx, first order), the shock sits within 1e-3 of the exact
+    position and L1(rho) falls with the mesh."""
+    from oracle import riemann
+    L = riemann.State(*inputs.SOD_LEFT)
+    R = riemann.State(*inputs.SOD_RIGHT)
+    st = riemann.solve_star(L, R)
+    res = []
+    for n in (256, 512, 1024, 2048):
+        p = inputs.sod_params(n)
+        dom = lbm.Domain(p)
+        dom.init_riemann(0, n // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+        steps = inputs.sod_steps(dom.dt)
+        dom.step(steps)
+        dom.synchronize()
+        rho = dom.primitives()[0, 0, 0]
+        t = steps * dom.dt
+        dom.close()
+        x = (np.arange(n) + 0.5) / n
+        re, _, _ = riemann.sample(L, R, (x - 0.5) / t)
+        right = x[:-1] > 0.5 + st.u * t + 0.05
+        w = (st.rho_R - R.rho) / (np.abs(np.diff(rho)) * n)[right].max()
+        mid = 0.5 * (st.rho_R + R.rho)
+        i = np.where(right & (rho[:-1] >= mid) & (rho[1:] < mid))[0][-1]
+        xs = x[i] + (rho[i] - mid) / (rho[i] - rho[i + 1]) / n
+        res.append(dict(n=n, w=w, xs=xs, xe=riemann.shock_position(L, R, t, 0.5),
+                        l1=float(np.mean(np.abs(rho - re)))))
+    for a, b in zip(res, res[1:]):
+        assert 1.6 < a["w"] / b["w"] < 2.5, res
+        assert b["l1"] < 0.8 * a["l1"], res
+    for r in res[1:]:
+        assert abs(r["xs"] - r["xe"]) < 1e-3, res
+        assert 3.0 < r["w"] * r["n"] < 9.0, res
+    print(res)
+
+
+def test_reduced_storage_at_128(lbm, oracle_mod):
+    """FP16 / BF16 shifted storage with FP32 arithmetic against the FP64 oracle and the
+    FP32 GPU path, TGV 128^3 after 60 steps; errors of rho, u, T and of the
+    diagnostics are stated (printed) and bounded."""
+    n, steps = 128, 60
+    p = inputs.tgv_params(n)
+    o = make_oracle(p)
+    o.init_tgv(1.0, 1.25, 1.0)
+    o.step(steps)
+    ref = o.primitives()
+    dref = o.diag()
+    out = {}
+    for store in ("f32", "f16", "bf16"):
+        d = lbm.Domain(p, store=store)
+        d.init_tgv(1.0, 1.25, 1.0)
+        d.step(steps)
+        g = d.primitives()
+        dg = d.diag()
+        d.close()
+        out[store] = {"rho": rel_l2(g[0], ref[0]), "u": rel_l2(g[1:4], ref[1:4]),
+                      "T": rel_l2(g[4], ref[4]),
+                      "ek": abs(dg["ek_mean"] / dref["ek_mean"] - 1),
+                      "eps_s": abs(dg["eps_s_raw"] / dref["eps_s_raw"] - 1),
+                      "eps_d": abs(dg["eps_d_raw"] / dref["eps_d_raw"] - 1)}
+    print(out)
+    assert max(out["f32"][k] for k in ("rho", "u", "T")) < 1e-5
+    assert max(out["f16"][k] for k in ("rho", "u", "T")) < 2e-3
+    assert max(out["bf16"][k] for k in ("rho", "u", "T")) < 2e-2
+    assert out["f16"]["ek"] < 1e-3 and out["bf16"]["ek"] < 1e-2
