@@ -267,18 +267,18 @@ def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
     return ms, clocks
 
 
-def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64):
+def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32"):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
     per domain per step."""
     doms = inputs.batch_domains()[:n_domains]
     pl = inputs.batch_params(doms)
-    B = lbm.Batch([q for q, _ in pl])
+    B = lbm.Batch([q for q, _ in pl], store=store)
     ic = [[c["U0"] for _, c in pl], [c["M0"] for _, c in pl], [c["rho0"] for _, c in pl]]
     B.init_tgv(*ic)
     tune = B.autotune(4)
     cells = B.total_cells()
-    out = {"domains": len(doms), "cells": cells, "tune": tune}
+    out = {"domains": len(doms), "cells": cells, "store": store, "tune": tune}
     for name, fn in (("persistent", B.step), ("sequential", B.step_sequential)):
         B.init_tgv(*ic)
         fn(warmup)
@@ -293,7 +293,7 @@ def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64):
         B.synchronize()
         out[name] = {"value": round(cells / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
                      "ms_per_step": round(ms, 4),
-                     "achieved_gbs": round(784 * cells / (ms * 1e-3) / 1e9, 1)}
+                     "achieved_gbs": round(BYTES_PER_CELL[store] * cells / (ms * 1e-3) / 1e9, 1)}
     B.close()
     return out
 
@@ -382,6 +382,8 @@ def run_gpu(args):
                             "steps": k2, "stated_err": stated_error(st)}
         variants[args.store] = {"stated_err": stated_error(args.store), "tune": tune}
         variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
+        variants["batch64_f16"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup,
+                                            store="f16")
 
     cpu = cpu_baseline(n) if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank == 0:

@@ -273,8 +273,8 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
 
 /* ---- many independent domains (batched mode) -------------------------------------
- * n periodic domains with their own sizes and parameters (F32 storage), stored in
- * one buffer. lbm_batch_step advances all of them by one step per persistent launch
+ * n periodic domains with their own sizes and parameters (one storage type for all,
+ * F32, F16 or BF16), stored in one buffer. lbm_batch_step advances all of them by one step per persistent launch
  * (grid = the resident blocks of the GPU; each warp takes items of consecutive
  * 32-cell tiles across all domains, the domain constants staged in shared memory),
  * replayed from a CUDA graph; lbm_batch_step_sequential issues one plain launch per

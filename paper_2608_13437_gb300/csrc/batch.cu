@@ -21,9 +21,9 @@ using namespace lbm;
 namespace lbm {
 namespace {
 
-template <int PARITY, int MINB>
+template <int PARITY, int MINB, typename S>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
-                                                          float* const* __restrict__ pops,
+                                                          void* const* __restrict__ pops,
                                                           const int* __restrict__ tile_prefix,
                                                           int ndom, int total_tiles,
                                                           int tiles_per_item,
@@ -31,14 +31,14 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
                                                           unsigned* __restrict__ flag) {
   extern __shared__ __align__(16) unsigned char smem[];
   DomainConst* sP = reinterpret_cast<DomainConst*>(smem);
-  float** sPop = reinterpret_cast<float**>(sP + ndom);
+  S** sPop = reinterpret_cast<S**>(sP + ndom);
   int* sPrefix = reinterpret_cast<int*>(sPop + ndom);
   {
     const int words = ndom * (int)(sizeof(DomainConst) / 4);
     const int* src = reinterpret_cast<const int*>(consts);
     int* dst = reinterpret_cast<int*>(sP);
     for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
-    for (int j = threadIdx.x; j < ndom; j += blockDim.x) sPop[j] = pops[j];
+    for (int j = threadIdx.x; j < ndom; j += blockDim.x) sPop[j] = static_cast<S*>(pops[j]);
     for (int j = threadIdx.x; j <= ndom; j += blockDim.x) sPrefix[j] = tile_prefix[j];
   }
   __syncthreads();
@@ -79,12 +79,12 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
         }
       }
       const CellIndex c = make_index(P, x, y, z);
-      float* pop = sPop[lo];
+      S* pop = sPop[lo];
       float d[kF][kQ];
-      load_cell<PARITY, false, float>(P, pop, nullptr, c, d);
+      load_cell<PARITY, false, S>(P, pop, nullptr, c, d);
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
-      store_cell<PARITY, float>(P, pop, c, d);
+      store_cell<PARITY, S>(P, pop, c, d);
     }
     item = (int)__shfl_sync(0xffffffffu, claim, 0);
   }
@@ -101,8 +101,10 @@ struct lbm_batch {
   std::vector<size_t> offset;   // byte offset of each domain's populations
   long long total_cells = 0;
   void* pool = nullptr;
+  int store = LBM_STORE_F32;
   DomainConst* d_consts = nullptr;
-  float** d_pops = nullptr;
+  void** d_pops = nullptr;
+  unsigned* d_maxbits = nullptr;  // per-field maxima for the FP16 scales at init
   int* d_prefix = nullptr;     // per-domain prefix sums of 32-cell tiles (n + 1)
   unsigned* d_counter = nullptr;  // work-item counter of the persistent kernel
   int total_tiles = 0;
@@ -131,24 +133,38 @@ namespace {
       return fail(LBM_E_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));                \
   } while (0)
 
-float* domain_pop(lbm_batch* b, int d) {
-  return reinterpret_cast<float*>(static_cast<char*>(b->pool) + b->offset[d]);
+void* domain_pop(lbm_batch* b, int d) { return static_cast<char*>(b->pool) + b->offset[d]; }
+
+template <int P, int M, typename S>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(k_batch_step<P, M, S>);
 }
 
-template <int P, int M>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(k_batch_step<P, M>);
+template <typename S>
+cudaError_t set_smem(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<0, 3, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 3, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<0, 4, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 4, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+template <typename S>
+void* any_kernel(int variant) {
+  return variant ? kernel_ptr<0, 4, S>() : kernel_ptr<0, 3, S>();
 }
 
 // Grid size for the current block size and register budget: every block resident.
 lbm_status size_grid(lbm_batch* b) {
   int per_sm = 0;
-  void* fn = b->variant ? kernel_ptr<0, 4>() : kernel_ptr<0, 3>();
+  void* fn = b->store == LBM_STORE_F32 ? any_kernel<float>(b->variant)
+             : b->store == LBM_STORE_F16 ? any_kernel<__half>(b->variant)
+                                         : any_kernel<__nv_bfloat16>(b->variant);
   if (b->smem > 48 * 1024) {
-    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<0, 3>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<1, 3>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<0, 4>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    LBM_CUDA(cudaFuncSetAttribute(kernel_ptr<1, 4>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    cudaError_t e = b->store == LBM_STORE_F32 ? set_smem<float>(b->smem)
+                    : b->store == LBM_STORE_F16 ? set_smem<__half>(b->smem)
+                                                : set_smem<__nv_bfloat16>(b->smem);
+    LBM_CUDA(e);
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, b->smem);
   if (e != cudaSuccess || per_sm < 1) return fail(LBM_E_CUDA, "batched kernel does not fit on an SM");
@@ -162,18 +178,25 @@ lbm_status size_grid(lbm_batch* b) {
   return LBM_OK;
 }
 
+template <typename S>
+void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
+  const dim3 g(b->grid), bl(b->block);
+  if (b->variant) {
+    if (parity) k_batch_step<1, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+  } else {
+    if (parity) k_batch_step<1, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+  }
+}
+
 // One persistent launch: zero the work-item counter, then the kernel.
 cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  const dim3 g(b->grid), bl(b->block);
-  if (b->variant) {
-    if (parity) k_batch_step<1, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 4><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-  } else {
-    if (parity) k_batch_step<1, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 3><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-  }
+  if (b->store == LBM_STORE_F32) launch_typed<float>(b, parity, s);
+  else if (b->store == LBM_STORE_F16) launch_typed<__half>(b, parity, s);
+  else launch_typed<__nv_bfloat16>(b, parity, s);
   return cudaGetLastError();
 }
 
@@ -215,6 +238,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return fail(LBM_E_NOMEM, "host allocation failed");
   b->n = n;
+  b->store = params[0].store;
   size_t bytes = 0;
   for (int d = 0; d < n; ++d) {
     lbm_status s = validate(&params[d]);
@@ -222,9 +246,9 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       delete b;
       return fail(s, "domain %d: %s", d, g_last_error.c_str());
     }
-    if (params[d].store != LBM_STORE_F32 || params[d].bc_x != 0) {
+    if (params[d].bc_x != 0 || params[d].store != params[0].store) {
       delete b;
-      return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic F32 domains", d);
+      return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
     }
     b->prm.push_back(params[d]);
     double dt, tR, tq;
@@ -238,7 +262,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     b->rho_ref.push_back(0.0);
     b->E_ref.push_back(0.0);
     b->offset.push_back(bytes);
-    bytes += (size_t)P.ntile * kP * kTile * sizeof(float);
+    bytes += (size_t)P.ntile * kP * kTile * elem_size(params[0].store);
     b->total_cells += P.ncell;
   }
   b->stream = static_cast<cudaStream_t>(params[0].cuda_stream);
@@ -251,22 +275,23 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     b->pool = nullptr;
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of %zu batch bytes failed", bytes));
   }
-  std::vector<float*> ptrs(n);
+  std::vector<void*> ptrs(n);
   for (int d = 0; d < n; ++d) ptrs[d] = domain_pop(b, d);
   std::vector<int> prefix(n + 1, 0);
   for (int d = 0; d < n; ++d) prefix[d + 1] = prefix[d] + (int)b->P[d].ntile;
   b->total_tiles = prefix[n];
-  b->smem = sizeof(DomainConst) * n + sizeof(float*) * n + sizeof(int) * (n + 1);
+  b->smem = sizeof(DomainConst) * n + sizeof(void*) * n + sizeof(int) * (n + 1);
   if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
-      cudaMalloc(&b->d_pops, sizeof(float*) * n) != cudaSuccess ||
+      cudaMalloc(&b->d_pops, sizeof(void*) * n) != cudaSuccess ||
+      cudaMalloc(&b->d_maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&b->d_prefix, sizeof(int) * (n + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_counter, 64) != cudaSuccess ||
       cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
   }
-  if (cudaMemcpy(b->d_pops, ptrs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMemcpy(b->d_pops, ptrs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "batch table upload failed"));
@@ -289,6 +314,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->d_pops) cudaFree(b->d_pops);
   if (b->d_prefix) cudaFree(b->d_prefix);
   if (b->d_counter) cudaFree(b->d_counter);
+  if (b->d_maxbits) cudaFree(b->d_maxbits);
   if (b->flag) cudaFree(b->flag);
   if (b->ghost) cudaFree(b->ghost);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -322,7 +348,22 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
     sp.c = p.dx / b->dt[d];
     sp.dx = p.dx;
     sp.sutherland = p.sutherland;
-    LBM_CUDA(launch_init(b->P[d], LBM_STORE_F32, sp, 1, domain_pop(b, d), nullptr, nullptr, b->stream));
+    for (int k = 0; k < kF; ++k) b->P[d].scale[k] = b->P[d].inv_scale[k] = 1.0f;
+    if (b->store == LBM_STORE_F16) {  // per-field scale max|f - w Q_ref| / 1024, as for one domain
+      LBM_CUDA(cudaMemsetAsync(b->d_maxbits, 0, kF * sizeof(unsigned), b->stream));
+      LBM_CUDA(launch_init(b->P[d], b->store, sp, 0, domain_pop(b, d), nullptr, b->d_maxbits, b->stream));
+      unsigned bits[kF];
+      LBM_CUDA(cudaMemcpyAsync(bits, b->d_maxbits, sizeof(bits), cudaMemcpyDeviceToHost, b->stream));
+      LBM_CUDA(cudaStreamSynchronize(b->stream));
+      for (int k = 0; k < kF; ++k) {
+        float m;
+        std::memcpy(&m, &bits[k], sizeof(m));
+        const float sk = (std::isfinite(m) && m > 0.0f) ? m / 1024.0f : 1.0f;
+        b->P[d].scale[k] = sk;
+        b->P[d].inv_scale[k] = 1.0f / sk;
+      }
+    }
+    LBM_CUDA(launch_init(b->P[d], b->store, sp, 1, domain_pop(b, d), nullptr, nullptr, b->stream));
   }
   lbm_status s = upload_consts(b);
   if (s != LBM_OK) return s;
@@ -367,7 +408,7 @@ lbm_status lbm_batch_step_sequential(lbm_batch* b, int n) {
     const int parity = (int)(b->step & 1);
     for (int d = 0; d < b->n; ++d) {
       const int bx = std::min(128, ((b->P[d].nx + 31) / 32) * 32);
-      LBM_CUDA(launch_step(b->P[d], LBM_STORE_F32, parity, domain_pop(b, d), b->ghost, b->flag, bx, 1,
+      LBM_CUDA(launch_step(b->P[d], b->store, parity, domain_pop(b, d), b->ghost, b->flag, bx, 1,
                            b->stream));
     }
     b->step += 1;
@@ -402,7 +443,7 @@ lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int
       return fail(LBM_E_NOMEM, "staging allocation failed");
     }
   }
-  cudaError_t e = launch_moments(P, LBM_STORE_F32, (int)(b->step & 1), domain_pop(b, domain), b->ghost,
+  cudaError_t e = launch_moments(P, b->store, (int)(b->step & 1), domain_pop(b, domain), b->ghost,
                                  which, dev, dtype == LBM_DT_F64, 0, P.ncell, b->stream);
   if (e == cudaSuccess && !dst_on_device)
     e = cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, b->stream);

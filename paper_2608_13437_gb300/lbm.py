@@ -307,9 +307,9 @@ class Domain:
 
 
 class Batch:
-    """Many independent periodic F32 domains advanced together."""
+    """Many independent periodic domains (one storage type) advanced together."""
 
-    def __init__(self, param_list: list[dict], device=None):
+    def __init__(self, param_list: list[dict], store="f32", device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -317,7 +317,7 @@ class Batch:
             self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
         self.stream = torch.cuda.current_stream(self.device)
-        arr = (LbmParams * len(param_list))(*[make_params(p, "f32", stream=self.stream.cuda_stream)
+        arr = (LbmParams * len(param_list))(*[make_params(p, store, stream=self.stream.cuda_stream)
                                               for p in param_list])
         h = ctypes.c_void_p()
         check(lib().lbm_batch_create(len(param_list), arr, ctypes.byref(h)))
