@@ -230,7 +230,7 @@ lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out);
  * for example because a memory pool already holds the free device memory or
  * because cudaMalloc's device-wide synchronisation is not acceptable there).
  * Same results as lbm_diag. Its scratch is a fixed device array inside the
- * library (about 8.3 MiB on every device that loads the library, kept until the
+ * library (about 4.2 MiB on every device that loads the library, kept until the
  * process exits), so it handles domains of at most 262144 cells (64^3) and returns
  * LBM_E_INVAL for larger ones. The first call on a device looks up the array's
  * device address (with that device current); make that first call before any

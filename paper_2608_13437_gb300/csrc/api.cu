@@ -142,7 +142,7 @@ struct lbm_handle {
   int variant = 0;             // register budget of the step kernel (see launch_step_t)
   cudaGraphExec_t g_pair = nullptr, g_chunk = nullptr;
   bool graphs_valid = false;
-  double* ufield = nullptr;
+  float* ufield = nullptr;     // diagnostics scratch: 4 floats per cell
   double* partials = nullptr;
   double* dout = nullptr;
 };
@@ -569,14 +569,15 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
 lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
   if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
   if (!h->ufield) {
-    if (cudaMalloc(&h->ufield, sizeof(double) * 4 * (size_t)h->ncell) != cudaSuccess ||
+    if (cudaMalloc(&h->ufield, sizeof(float) * 4 * (size_t)h->ncell) != cudaSuccess ||
         cudaMalloc(&h->partials, sizeof(double) * (size_t)kDiagBlocks * (kDiagA + 2)) != cudaSuccess ||
         cudaMalloc(&h->dout, sizeof(double) * 16) != cudaSuccess) {
       cudaGetLastError();
       if (h->ufield) cudaFree(h->ufield);
       if (h->partials) cudaFree(h->partials);
       if (h->dout) cudaFree(h->dout);
-      h->ufield = h->partials = h->dout = nullptr;
+      h->ufield = nullptr;
+      h->partials = h->dout = nullptr;
       return fail(LBM_E_NOMEM, "diagnostic scratch allocation failed");
     }
   }

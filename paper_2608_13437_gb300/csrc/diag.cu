@@ -1,7 +1,9 @@
-// FP64 diagnostics of the current state (Sec. 3.2, Eq. 7): conservation sums,
+// Diagnostics of the current state (Sec. 3.2, Eq. 7): conservation sums,
 // <rho|u|^2/2>, <mu_local |curl u|^2>, 4/3 <mu_local (div u)^2>, extrema and a
-// non-finite count. Pass A decodes every cell (FP64) and keeps u and mu_local in
-// a scratch field; pass B takes central differences of u from that field; each
+// non-finite count. Per-cell work runs in FP32 exactly as in the step; FP64 is used
+// for the sums, extrema and differences. Pass A decodes every cell and keeps u and
+// mu_local in a scratch field (4 floats per cell); pass B takes central differences of
+// u from that field; each
 // pass writes one partial per block (warp shuffles, then shared memory), and a
 // single block reduces the partials in a fixed order, so results are
 // reproducible run to run.
@@ -46,68 +48,70 @@ __device__ void block_reduce(double (&v)[N], int nsum, int nmax, double* out) {
   }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kBlock) k_diag_a(const DomainConst P, int parity,
-                                                   const S* __restrict__ pop,
+// Pass A: per cell, the step's own FP32 decode, moments and closure; FP64 only for the
+// running sums, extrema and counts. Writes u and mu_local (FP32) for pass B.
+template <typename S, int PARITY, bool HELD>
+__global__ void __launch_bounds__(kBlock) k_diag_a(const DomainConst P, const S* __restrict__ pop,
                                                    const float* __restrict__ ghost,
-                                                   double* __restrict__ ufield,
+                                                   float* __restrict__ ufield,
                                                    double* __restrict__ partials) {
   double acc[kDiagA];
-  for (int j = 0; j < 7; ++j) acc[j] = 0.0;
-  acc[7] = acc[8] = 0.0;            // max mach, max cfl
-  acc[9] = acc[10] = INFINITY;      // min rho, min T
-  acc[11] = acc[12] = 0.0;          // spare sums (zero)
+  for (int j = 0; j < 9; ++j) acc[j] = 0.0;  // rho mx my mz E ke nonfinite, 2 spare
+  acc[9] = acc[10] = 0.0;                    // max mach, max cfl
+  acc[11] = acc[12] = INFINITY;              // min rho, min T
+  const double c64 = P.dx64 / P.dt64;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(cell % P.nx);
     const long long yz = cell / P.nx;
     const CellIndex c = make_index(P, x, (int)(yz % P.ny), (int)(yz / P.ny));
-    double Q[kF];
+    float d[kF][kQ];
+    load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
+    float D[kF];
     bool finite = true;
+#pragma unroll
     for (int k = 0; k < kF; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < kQ; ++i) {
-        const double v = from_ghost(P, c, i)
-                             ? (double)ghost_value(P, ghost, c, k, i)
-                             : Codec<S>::dec64(pop[read_pos(P, c, parity, k, i)], (double)P.scale[k]);
-        s += v;
-      }
-      Q[k] = s;
+      float t = d[k][0];
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) t = add(t, d[k][i]);
+      D[k] = t;
+      finite = finite && isfinite(t);
     }
-    Q[0] += (double)P.rho_ref;
-    Q[4] += (double)P.E_ref;
-    for (int k = 0; k < kF; ++k) finite = finite && isfinite(Q[k]);
-    Prim<double> s;
-    closure<double>(Q, P.gm1_64, P.mu64, 0.0, 0.0, P.inv_T_ref64, P.sutherland, s);
-    acc[0] += Q[0];
-    acc[1] += Q[1];
-    acc[2] += Q[2];
-    acc[3] += Q[3];
-    acc[4] += Q[4];
-    acc[5] += 0.5 * (s.m[0] * s.u[0] + s.m[1] * s.u[1] + s.m[2] * s.u[2]);
+    float Q[kF];
+#pragma unroll
+    for (int k = 0; k < kF; ++k) Q[k] = D[k];
+    Q[0] = add(Q[0], P.rho_ref);
+    Q[4] = add(Q[4], P.E_ref);
+    Prim<float> s;
+    closure<float>(Q, P.gm1, P.mu, P.visc0, P.heat0, P.inv_T_ref, P.sutherland, s);
+    // reference + deviation in FP64, so the totals keep the deviations' precision
+    acc[0] += (double)P.rho_ref + (double)D[0];
+    acc[1] += (double)D[1];
+    acc[2] += (double)D[2];
+    acc[3] += (double)D[3];
+    acc[4] += (double)P.E_ref + (double)D[4];
+    acc[5] += 0.5 * ((double)s.m[0] * s.u[0] + (double)s.m[1] * s.u[1] + (double)s.m[2] * s.u[2]);
     acc[6] += finite ? 0.0 : 1.0;
-    const double a = sqrt((P.gm1_64 + 1.0) * s.T);
-    const double umag = sqrt(s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
-    const double umax = fmax(fabs(s.u[0]), fmax(fabs(s.u[1]), fabs(s.u[2])));
     if (finite) {
-      acc[7] = fmax(acc[7], umag / a);
-      acc[8] = fmax(acc[8], (umax + a) * P.dt64 / P.dx64);  // (|u_a| + a) dt / dx
-      acc[9] = fmin(acc[9], s.rho);
-      acc[10] = fmin(acc[10], s.T);
+      const double a = sqrt((P.gm1_64 + 1.0) * (double)s.T);
+      const double ux = s.u[0], uy = s.u[1], uz = s.u[2];
+      acc[9] = fmax(acc[9], sqrt(ux * ux + uy * uy + uz * uz) / a);
+      acc[10] = fmax(acc[10], (fmax(fabs(ux), fmax(fabs(uy), fabs(uz))) + a) / c64);  // (|u_a|+a) dt/dx
+      acc[11] = fmin(acc[11], (double)s.rho);
+      acc[12] = fmin(acc[12], (double)s.T);
     }
     ufield[cell] = s.u[0];
     ufield[P.ncell + cell] = s.u[1];
     ufield[2 * P.ncell + cell] = s.u[2];
     ufield[3 * P.ncell + cell] = s.mu_T;
   }
-  // partial layout: 9 sums (rho, mx, my, mz, E, ke, nonfinite, 0, 0), 2 maxima, 2 minima
-  double v[kDiagA] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], acc[11], acc[12],
-                      acc[7], acc[8], acc[9], acc[10]};
-  block_reduce<kDiagA>(v, 9, 2, partials + (long long)blockIdx.x * kDiagA);
+  block_reduce<kDiagA>(acc, 9, 2, partials + (long long)blockIdx.x * kDiagA);
 }
 
+// Pass B: central differences of u (FP64 differences of the FP32 field), weighted by
+// mu_local, summed in FP64.
 __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
-                                                   const double* __restrict__ ufield,
+                                                   const float* __restrict__ ufield,
                                                    double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
   const long long n = P.ncell;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
         span = (double)((x < P.nx - 1) + (x > 0));
       }
       for (int b = 0; b < 3; ++b)
-        g[a][b] = span > 0.0 ? (ufield[b * n + hi] - ufield[b * n + lo]) / (span * P.dx64)
+        g[a][b] = span > 0.0 ? ((double)ufield[b * n + hi] - (double)ufield[b * n + lo]) / (span * P.dx64)
                              : 0.0;
     }
     const double wx = g[1][2] - g[2][1], wy = g[2][0] - g[0][2], wz = g[0][1] - g[1][0];
@@ -136,8 +140,7 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
     acc[0] += mu_loc * (wx * wx + wy * wy + wz * wz);
     acc[1] += mu_loc * div * div;
   }
-  double v[2] = {acc[0], acc[1]};
-  block_reduce<2>(v, 2, 0, partials + (long long)blockIdx.x * 2);
+  block_reduce<2>(acc, 2, 0, partials + (long long)blockIdx.x * 2);
 }
 
 // Fixed-order reduction of the partials of both passes (one block).
@@ -159,21 +162,39 @@ __global__ void k_diag_final(const double* __restrict__ pa, const double* __rest
   }
 }
 
+template <typename S, int PARITY, bool HELD>
+void launch_a(const DomainConst& P, const void* pop, const float* ghost, float* ufield, double* pa,
+              cudaStream_t s) {
+  k_diag_a<S, PARITY, HELD><<<kDiagBlocks, kBlock, 0, s>>>(P, static_cast<const S*>(pop), ghost,
+                                                           ufield, pa);
+}
+
+template <typename S>
+void launch_a_store(const DomainConst& P, int parity, const void* pop, const float* ghost,
+                    float* ufield, double* pa, cudaStream_t s) {
+  if (P.bc_x) {
+    if (parity) launch_a<S, 1, true>(P, pop, ghost, ufield, pa, s);
+    else launch_a<S, 0, true>(P, pop, ghost, ufield, pa, s);
+  } else {
+    if (parity) launch_a<S, 1, false>(P, pop, ghost, ufield, pa, s);
+    else launch_a<S, 0, false>(P, pop, ghost, ufield, pa, s);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void* pop,
-                        const float* ghost, double* ufield, double* partials, double* out16,
+                        const float* ghost, float* ufield, double* partials, double* out16,
                         cudaStream_t s) {
-  const int nb = kDiagBlocks;
   double* pa = partials;
-  double* pb = partials + (long long)nb * kDiagA;
+  double* pb = partials + (long long)kDiagBlocks * kDiagA;
   switch (store) {
-    case 0: k_diag_a<float><<<nb, kBlock, 0, s>>>(P, parity, (const float*)pop, ghost, ufield, pa); break;
-    case 1: k_diag_a<__half><<<nb, kBlock, 0, s>>>(P, parity, (const __half*)pop, ghost, ufield, pa); break;
-    default: k_diag_a<__nv_bfloat16><<<nb, kBlock, 0, s>>>(P, parity, (const __nv_bfloat16*)pop, ghost, ufield, pa); break;
+    case 0: launch_a_store<float>(P, parity, pop, ghost, ufield, pa, s); break;
+    case 1: launch_a_store<__half>(P, parity, pop, ghost, ufield, pa, s); break;
+    default: launch_a_store<__nv_bfloat16>(P, parity, pop, ghost, ufield, pa, s); break;
   }
-  k_diag_b<<<nb, kBlock, 0, s>>>(P, ufield, pb);
-  k_diag_final<<<1, 32, 0, s>>>(pa, pb, nb, out16);
+  k_diag_b<<<kDiagBlocks, kBlock, 0, s>>>(P, ufield, pb);
+  k_diag_final<<<1, 32, 0, s>>>(pa, pb, kDiagBlocks, out16);
   return cudaGetLastError();
 }
 

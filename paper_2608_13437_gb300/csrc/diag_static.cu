@@ -31,12 +31,12 @@ namespace lbm {
 namespace {
 
 constexpr long long kStaticDiagMaxCells = 262144;  // 64^3
-constexpr long long kStaticU = 4 * kStaticDiagMaxCells;                  // u and mu_local
+constexpr long long kStaticU = 2 * kStaticDiagMaxCells;  // u and mu_local: 4 floats per cell
 constexpr long long kStaticPartials = (long long)kDiagBlocks * (kDiagA + 2);
 constexpr long long kStaticOut = 16;
 constexpr long long kStaticDoubles = kStaticU + kStaticPartials + kStaticOut;
 
-// About 8.3 MiB of device memory per device.
+// About 4.2 MiB of device memory per device.
 static __device__ __align__(256) double g_static_diag_scratch[kStaticDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -77,7 +77,7 @@ extern "C" lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out) {
   double* base = nullptr;
   lbm_status s = scratch_address(&base);
   if (s != LBM_OK) return s;
-  double* ufield = base;
+  float* ufield = reinterpret_cast<float*>(base);
   double* partials = base + kStaticU;
   double* dout = partials + kStaticPartials;
   // The scratch is sized for kStaticDiagMaxCells; the kernels index it by this

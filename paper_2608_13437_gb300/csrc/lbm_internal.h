@@ -52,8 +52,9 @@ cudaError_t launch_pop_set(const DomainConst& P, int store, int parity, void* po
 // Diagnostics (diag.cu).
 constexpr int kDiagA = 13;  // sums: rho mx my mz E ke nonfinite | max: mach cfl | min: rho T
 constexpr int kDiagBlocks = 1216;
+// ufield: 4 floats per cell of scratch; partials: kDiagBlocks * (kDiagA + 2) doubles.
 cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void* pop,
-                        const float* ghost, double* ufield, double* partials, double* out16,
+                        const float* ghost, float* ufield, double* partials, double* out16,
                         cudaStream_t s);
 
 }  // namespace lbm
