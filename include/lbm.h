@@ -191,6 +191,12 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
  * mean of p/(gamma-1) + rho|u|^2/2). */
 lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype);
 
+/* Equilibrium from caller zeroth moments [14][cells] (rho, rho u, E, tau, q; the
+ * field order above) in `dtype` on the host or the device, e.g. a state whose stress
+ * and heat flux start at their Newtonian and Fourier values (Becker's shock,
+ * Sec. 3.1). Q_ref = (mean rho, 0, 0, 0, mean E). */
+lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int dtype);
+
 /* ---- the hot path ------------------------------------------------------------ */
 
 /* Advances n >= 0 time steps: per step one fused kernel reads each cell's 98

@@ -510,6 +510,24 @@ int orc_init_fields(void* h, const double* rho, const double* ux, const double* 
   return 0;
 }
 
+// Equilibrium initialisation from given zeroth moments Q[k][cell] (all 14 fields).
+int orc_init_state(void* h, const double* Qin) {
+  Domain& d = *static_cast<Domain*>(h);
+#pragma omp parallel for schedule(static)
+  for (int64_t cl = 0; cl < d.ncell; ++cl) {
+    double Q[NF];
+    for (int k = 0; k < NF; ++k) Q[k] = Qin[(int64_t)k * d.ncell + cl];
+    const Closure c = closure(d.p, Q);
+    double Phi[NF][3], feq[NF][NQ];
+    flux(d.p, Q, c, Phi);
+    equilibrium(d.c, Q, Phi, feq);
+    for (int k = 0; k < NF; ++k)
+      for (int i = 0; i < NQ; ++i) d.at(d.f, k, i, cl) = feq[k][i];
+  }
+  finish_init(d);
+  return 0;
+}
+
 // Canonical populations f[k][i][cell] (pre-collision state).
 void orc_get_populations(void* h, double* out) {
   Domain& d = *static_cast<Domain*>(h);

@@ -84,6 +84,7 @@ def lib():
                                        ip, ip, ip, ip]
             L.orc_init_riemann.argtypes = [vp, ip, ip, dp, dp]
             L.orc_init_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+            L.orc_init_state.argtypes = [vp, dp]
             L.orc_get_populations.argtypes = [vp, dp]
             L.orc_set_populations.argtypes = [vp, dp]
             L.orc_step.argtypes = [vp, ip]
@@ -177,6 +178,11 @@ class Oracle:
         arrs = [np.ascontiguousarray(np.broadcast_to(a, self.shape), dtype=np.float64)
                 for a in (rho, ux, uy, uz, p)]
         lib().orc_init_fields(self._h, *[_dp(a) for a in arrs])
+
+    def init_state(self, Q):
+        """Equilibrium of given zeroth moments Q (14, nz, ny, nx)."""
+        Q = np.ascontiguousarray(np.broadcast_to(Q, (NF,) + self.shape), dtype=np.float64)
+        lib().orc_init_state(self._h, _dp(Q))
 
     def step(self, n: int = 1):
         lib().orc_step(self._h, int(n))

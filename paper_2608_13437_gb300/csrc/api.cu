@@ -414,10 +414,11 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
   return run_init(h, sp);
 }
 
-lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype) {
+static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype,
+                                   int kind, int nfield) {
   if (!h || !fields) return fail(LBM_E_INVAL, "NULL argument");
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
-  const size_t bytes = (size_t)5 * h->ncell * (dtype == LBM_DT_F64 ? 8 : 4);
+  const size_t bytes = (size_t)nfield * h->ncell * (dtype == LBM_DT_F64 ? 8 : 4);
   void* dev = const_cast<void*>(fields);
   void* tmp = nullptr;
   if (!src_on_device) {
@@ -433,7 +434,7 @@ lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device,
     dev = tmp;
   }
   InitSpec sp{};
-  sp.kind = 2;
+  sp.kind = kind;
   sp.fields = dev;
   sp.fields_f64 = dtype == LBM_DT_F64;
   sp.gamma = h->prm.gamma;
@@ -454,6 +455,14 @@ lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device,
   }
   if (tmp) cudaFree(tmp);
   return st;
+}
+
+lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype) {
+  return init_from_fields(h, fields, src_on_device, dtype, 2, 5);
+}
+
+lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int dtype) {
+  return init_from_fields(h, Q, src_on_device, dtype, 3, kF);
 }
 
 lbm_status lbm_step(lbm_handle* h, int n) {

@@ -1,15 +1,26 @@
-// Initial states (Sec. 3): TGV, Riemann problem, caller fields. Each cell gets the
-// linear equilibrium of its state with tau = q = 0, computed in FP64 and stored as
-// the deviation from w_i Q_ref in the storage type.
+// Initial states (Sec. 3): TGV, Riemann problem, caller fields (rho, u, p) or caller
+// zeroth moments (all 14 fields). Each cell gets the linear equilibrium of its state
+// (tau = q = 0 unless given), computed in FP64 and stored as the deviation from
+// w_i Q_ref in the storage type.
 #include "lbm_internal.h"
 
 namespace lbm {
 
 namespace {
 
-// Macroscopic initial state (rho, u, p) of the cell.
-__device__ void initial_state(const DomainConst& P, const InitSpec& sp, int x, int y, int z,
-                              long long cell, double& rho, double u[3], double& p) {
+// Zeroth moments Q of the initial state of the cell: (rho, rho u, E) with tau = q = 0
+// for the TGV, Riemann and (rho, u, p)-field initial states, or all 14 fields given.
+__device__ void initial_Q(const DomainConst& P, const InitSpec& sp, int x, int y, int z,
+                          long long cell, double Q[kF]) {
+  for (int k = 0; k < kF; ++k) Q[k] = 0.0;
+  if (sp.kind == 3) {
+    const long long n = P.ncell;
+    for (int k = 0; k < kF; ++k)
+      Q[k] = sp.fields_f64 ? static_cast<const double*>(sp.fields)[k * n + cell]
+                           : (double)static_cast<const float*>(sp.fields)[k * n + cell];
+    return;
+  }
+  double rho, u[3], p;
   if (sp.kind == 0) {
     // Supersonic TGV (Sec. 3.2), nodes at (x, y, z) dx.
     const double X = x * sp.dx, Y = y * sp.dx, Z = z * sp.dx;
@@ -37,16 +48,14 @@ __device__ void initial_state(const DomainConst& P, const InitSpec& sp, int x, i
       rho = f[cell]; u[0] = f[n + cell]; u[1] = f[2 * n + cell]; u[2] = f[3 * n + cell]; p = f[4 * n + cell];
     }
   }
-}
-
-// Deviations d_{k,i} = feq_{k,i}(Q) - w_i Q_ref,k of the equilibrium with tau = q = 0.
-__device__ void equilibrium_dev(const DomainConst& P, const InitSpec& sp, double rho,
-                                const double u[3], double p, double dev[kF][kQ]) {
-  double Q[kF];
-  for (int k = 0; k < kF; ++k) Q[k] = 0.0;
   Q[0] = rho;
   for (int a = 0; a < 3; ++a) Q[1 + a] = rho * u[a];
   Q[4] = p / (sp.gamma - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// Deviations d_{k,i} = feq_{k,i}(Q) - w_i Q_ref,k of the linear equilibrium of Q.
+__device__ void equilibrium_dev(const DomainConst& P, const InitSpec& sp, const double Q[kF],
+                                double dev[kF][kQ]) {
   Prim<double> s;
   closure<double>(Q, sp.gamma - 1.0, sp.mu, sp.mu / sp.tau_R, sp.kappa / sp.tau_q, sp.inv_T_ref,
                   sp.sutherland, s);
@@ -76,10 +85,10 @@ __global__ void k_init(const DomainConst P, const InitSpec sp, int mode, S* __re
     const int x = (int)(cell % P.nx);
     const long long yz = cell / P.nx;
     const int y = (int)(yz % P.ny), z = (int)(yz / P.ny);
-    double rho, u[3], p;
-    initial_state(P, sp, x, y, z, cell, rho, u, p);
+    double Q[kF];
+    initial_Q(P, sp, x, y, z, cell, Q);
     double dev[kF][kQ];
-    equilibrium_dev(P, sp, rho, u, p, dev);
+    equilibrium_dev(P, sp, Q, dev);
     if (mode == 0) {
       for (int k = 0; k < kF; ++k) {
         float m = 0.0f;
@@ -105,10 +114,10 @@ __global__ void k_field_means(const DomainConst P, const InitSpec sp, double* su
   double s_rho = 0.0, s_E = 0.0;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
-    double rho, u[3], p;
-    initial_state(P, sp, 0, 0, 0, cell, rho, u, p);
-    s_rho += rho;
-    s_E += p / (sp.gamma - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double Q[kF];
+    initial_Q(P, sp, 0, 0, 0, cell, Q);
+    s_rho += Q[0];
+    s_E += Q[4];
   }
   for (int o = 16; o > 0; o >>= 1) {
     s_rho += __shfl_down_sync(0xffffffffu, s_rho, o);

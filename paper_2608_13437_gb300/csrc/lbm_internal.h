@@ -16,13 +16,14 @@ cudaError_t launch_step_f16(const DomainConst& P, int parity, void* pop, const f
 cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const float* ghost,
                              unsigned* flag, int block_x, int variant, cudaStream_t s);
 
-// Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields.
+// Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields (rho, u, p),
+// 3 caller zeroth moments (14 fields).
 struct InitSpec {
   int kind;
   double U0, M0, rho0;                 // TGV
   int axis, split;                     // Riemann
   double left[3], right[3];
-  const void* fields;                  // [5][cell] rho, ux, uy, uz, p on the device
+  const void* fields;                  // kind 2: [5][cell] rho, ux, uy, uz, p; kind 3: [14][cell] Q
   int fields_f64;
   double gamma, mu, kappa, tau_R, tau_q, inv_T_ref, c, dx;
   int sutherland;
@@ -31,7 +32,7 @@ struct InitSpec {
 // the encoded populations (canonical slots) and the held-x ghost layers.
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
                         float* ghost, unsigned* maxbits, cudaStream_t s);
-// Sums of rho and E = p/(gamma-1) + rho|u|^2/2 over caller fields into sums[2] (zeroed here).
+// Sums of rho and E over the caller fields (kind 2 or 3) into sums[2] (zeroed here).
 cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
                                cudaStream_t s);
 

@@ -94,6 +94,28 @@ def sod_steps(dt: float, t_end: float = 0.2) -> int:
     return int(round(t_end / dt))
 
 
+# Becker's viscous shock (Sec. 3.1): M_s = 2 into gas at rest (rho, c) = (1, 1), constant
+# mu = 2e-3 (Re_s = rho c M_s L / mu = 1000), Pr = 3/4, CFL 0.125, tau_R = tau_q = 5 dt,
+# shock centre at x = 0.25 of [0, 1] at t = 0, compared at t = 0.2.
+BECKER_MU = 2e-3
+BECKER_MACH = 2.0
+BECKER_X0 = 0.25
+# Largest |u| + a of the exact Becker solution (downstream state), written by
+# tests/golden/gen_golden.py from the oracle's Becker solver.
+BECKER_LAMBDA_MAX = 2.5490381056766580
+
+
+def becker_params(n: int, ny: int = 4, nz: int = 4, cfl: float = 0.125,
+                  relax_steps: float = 5.0) -> dict:
+    """Becker tube on [0, 1] with n cells along x (held ends), periodic y, z."""
+    cp = GAMMA / (GAMMA - 1.0)
+    return dict(
+        nx=n, ny=ny, nz=nz, dx=1.0 / n, bc_x=1, dt=0.0, cfl=cfl, lambda_ref=BECKER_LAMBDA_MAX,
+        gamma=GAMMA, mu=BECKER_MU, kappa=BECKER_MU * cp / 0.75, tau_R=relax_steps,
+        tau_q=relax_steps, relax_in_dt=1, T_ref=1.0, sutherland=0, source_mode=0, f_mu=0.0,
+        C_sigma=20.0, J_min=3e-3, omega_min=1.0, sensor_mode=0, collide=1)
+
+
 # ---------------------------------------------------------------------------
 # Seeded generators
 # ---------------------------------------------------------------------------

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "lbm_init_tgv": (_IP, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lbm_init_riemann": (_IP, [_VP, _IP, _IP, _DP, _DP]),
     "lbm_init_fields": (_IP, [_VP, _VP, _IP, _IP]),
+    "lbm_init_state": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_step": (_IP, [_VP, _IP]),
     "lbm_synchronize": (_IP, [_VP]),
     "lbm_moments": (_IP, [_VP, _IP, _VP, _IP, _IP]),
@@ -217,6 +218,12 @@ class Domain:
                                              (rho, ux, uy, uz, p)]), dtype=dtype)
         check(lib().lbm_init_fields(self._h, _np_ptr(arr), 0,
                                     DT_F64 if arr.dtype == np.float64 else DT_F32))
+
+    def init_state(self, Q, dtype=np.float64):
+        """Equilibrium of given zeroth moments Q (14, nz, ny, nx)."""
+        arr = np.ascontiguousarray(np.broadcast_to(Q, (14,) + self.shape), dtype=dtype)
+        check(lib().lbm_init_state(self._h, _np_ptr(arr), 0,
+                                   DT_F64 if arr.dtype == np.float64 else DT_F32))
 
     def init_fields_device(self, fields, src_on_device=True):
         """fields: torch tensor (5, nz, ny, nx) float32/float64 on the device (or pinned host)."""

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from oracle import riemann  # noqa: E402
+from oracle import becker, riemann  # noqa: E402
 
 SOD_LEFT = (1.0, 0.0, 1.0)
 SOD_RIGHT = (0.125, 0.0, 0.1)
@@ -29,6 +29,19 @@ def main():
         json.dump(out, fh, indent=1)
         fh.write("\n")
     print(json.dumps(out, indent=1))
+    b = becker.paper_case()
+    rho2, u2_lab, p2 = b.downstream()
+    bk = {
+        "_source": "oracle/becker.py exact Becker profile, gamma 1.4, Pr 3/4, mu 2e-3, M_s 2, "
+                   "upstream (rho, c) = (1, 1) (Sec. 3.1)",
+        "u1": b.u1, "u2": b.u2, "rho2": rho2, "u2_lab": u2_lab, "p2": p2,
+        "lambda_max": b.max_signal_speed(),
+        "w_max_slope_rho": b.thickness(),
+    }
+    with open(os.path.join(HERE, "becker_exact.json"), "w") as fh:
+        json.dump(bk, fh, indent=1)
+        fh.write("\n")
+    print(json.dumps(bk, indent=1))
 
 
 if __name__ == "__main__":

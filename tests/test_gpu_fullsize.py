@@ -125,3 +125,68 @@ def test_reduced_storage_at_128(lbm, oracle_mod):
     assert max(out["f16"][k] for k in ("rho", "u", "T")) < 2e-3
     assert max(out["bf16"][k] for k in ("rho", "u", "T")) < 2e-2
     assert out["f16"]["ek"] < 1e-3 and out["bf16"]["ek"] < 1e-2
+
+
+def test_becker_gpu_convergence_and_paper_table3(lbm, oracle_mod):
+    """Becker's shock on 750, 1500, 3000 x 4 x 4 cells (x ends held): the GPU profile
+    matches the oracle's at N = 750 (shock position, mean difference); L1(rho) and L1(p)
+    within 25 % of Table 3 at N = 750 and no larger than the paper's beyond; the excess
+    thickness w / w_ex - 1 falls at least at first order (Table 2). (At N = 6000 the
+    stress and heat-flux relaxation waves, whose speed grows as dt^-1/2 with
+    tau_R = tau_q = 5 dt, reach 0.87 of the lattice sound speed under the CFL reading
+    used here, and oracle and GPU both diverge.)"""
+    import json
+    import os
+
+    from oracle import becker
+    b = becker.paper_case()
+    wex = b.thickness()
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    res = []
+    for n in (750, 1500, 3000):
+        p = inputs.becker_params(n)
+        dom = lbm.Domain(p)
+        dom.init_state(becker.initial_moments(b, n, 4, 4, inputs.BECKER_X0))
+        dt = dom.dt
+        steps = int(round(0.2 / dt))
+        dom.step(steps)
+        dom.synchronize()
+        P = dom.primitives()
+        dom.close()
+        rho = P[0, 0, 0]
+        t = steps * dt
+        x = (np.arange(n) + 0.5) / n
+        rho_e, _, _, _, _, _ = b.lab(x, t, inputs.BECKER_X0)
+        w = (b.downstream()[0] - b.rho1) / np.max(np.abs(np.diff(rho)) * n)
+        paper = next(r for r in gold["becker_conv"] if r["N"] == n)
+        _, _, p_e, _, _, _ = b.lab(x, t, inputs.BECKER_X0)
+        res.append(dict(n=n, l1=float(np.mean(np.abs(rho - rho_e))), excess=w / wex - 1,
+                        l1p=float(np.mean(np.abs(P[5, 0, 0] - p_e))), paper_l1=paper["L1_rho"],
+                        paper_l1p=paper["L1_p"]))
+        if n == 750:
+            # shocked flow: parity is the shock position (within 1e-3, as for Sod) and a
+            # small mean difference; at omega = 2 the undamped modes carry FP32 and FP64
+            # rounding apart locally near the front
+            o = make_oracle(inputs.becker_params(n, ny=1, nz=1))
+            o.init_state(becker.initial_moments(b, n, 1, 1, inputs.BECKER_X0))
+            o.step(steps)
+            rho_o = o.primitives()[0, 0, 0]
+            mid = 0.5 * (b.rho1 + b.downstream()[0])
+
+            def front(r):
+                i = np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]
+                return x[i] + (r[i] - mid) / (r[i] - r[i + 1]) / n
+
+            res[-1]["front_gpu_minus_oracle"] = front(rho) - front(rho_o)
+            res[-1]["mean_abs_diff_oracle"] = float(np.mean(np.abs(rho - rho_o)))
+            assert abs(front(rho) - front(rho_o)) < 1e-3
+            assert np.mean(np.abs(rho - rho_o)) < 1e-3
+    print(res)
+    assert res[0]["l1"] == pytest.approx(res[0]["paper_l1"], rel=0.25), res
+    assert res[0]["l1p"] == pytest.approx(res[0]["paper_l1p"], rel=0.25), res
+    for r in res[1:]:
+        assert r["l1"] <= 1.25 * r["paper_l1"], r
+    for a, c in zip(res, res[1:]):
+        assert a["excess"] / c["excess"] > 1.8, res
+        assert c["l1"] < 0.7 * a["l1"], res
+
