@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(kBlock) k_diag_a(const DomainConst P, const S*
   const double c64 = P.dx64 / P.dt64;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(cell % P.nx);
-    const long long yz = cell / P.nx;
-    const CellIndex c = make_index(P, x, (int)(yz % P.ny), (int)(yz / P.ny));
+    int x, y, z;
+    cell_xyz(P, cell, x, y, z);
+    const CellIndex c = make_index(P, x, y, z);
     float d[kF][kQ];
     load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
     float D[kF];
@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
   const long long n = P.ncell;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
        cell += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(cell % P.nx);
-    const long long yz = cell / P.nx;
-    const int y = (int)(yz % P.ny), z = (int)(yz / P.ny);
+    int x, y, z;
+    cell_xyz(P, cell, x, y, z);
     const CellIndex c = make_index(P, x, y, z);
     double g[3][3];  // g[a][b] = d_a u_b
     for (int a = 0; a < 3; ++a) {

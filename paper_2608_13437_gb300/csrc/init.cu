@@ -82,9 +82,9 @@ __global__ void k_init(const DomainConst P, const InitSpec sp, int mode, S* __re
   const long long planes = (long long)P.ny * P.nz;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
        cell += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(cell % P.nx);
-    const long long yz = cell / P.nx;
-    const int y = (int)(yz % P.ny), z = (int)(yz / P.ny);
+    int x, y, z;
+    cell_xyz(P, cell, x, y, z);
+    const long long yz = (long long)y + (long long)P.ny * z;  // ghost-plane index
     double Q[kF];
     initial_Q(P, sp, x, y, z, cell, Q);
     double dev[kF][kQ];

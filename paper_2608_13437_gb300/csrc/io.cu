@@ -9,10 +9,7 @@ namespace {
 
 __device__ __forceinline__ void decompose(const DomainConst& P, long long cell, int& x, int& y,
                                           int& z) {
-  x = (int)(cell % P.nx);
-  const long long yz = cell / P.nx;
-  y = (int)(yz % P.ny);
-  z = (int)(yz / P.ny);
+  cell_xyz(P, cell, x, y, z);
 }
 
 template <typename S>

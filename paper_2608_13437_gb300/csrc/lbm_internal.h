@@ -7,6 +7,18 @@
 
 namespace lbm {
 
+// (x, y, z) of a linear cell index; cell counts are below 2^31, so 32-bit unsigned
+// division suffices (much cheaper than 64-bit).
+__device__ __forceinline__ void cell_xyz(const DomainConst& P, long long cell, int& x, int& y,
+                                         int& z) {
+  const unsigned c = (unsigned)cell;
+  const unsigned yz = c / (unsigned)P.nx;
+  x = (int)(c - yz * (unsigned)P.nx);
+  const unsigned zz = yz / (unsigned)P.ny;
+  y = (int)(yz - zz * (unsigned)P.ny);
+  z = (int)zz;
+}
+
 // Fused step: one launch per time step, grid (ceil(nx/block_x), ny, nz), block_x in
 // {32, 64, 96, 128}; variant selects the register budget (0: 170, 1: 128 registers).
 cudaError_t launch_step_f32(const DomainConst& P, int parity, void* pop, const float* ghost,
