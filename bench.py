@@ -267,6 +267,27 @@ def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
     return ms, clocks
 
 
+def diag_costs(torch, dom, ms_step, reps=8):
+    """GPU time of one separate FP64 diagnostic pass (lbm_diag) and of one step that
+    computes the diagnostics itself (lbm_step_diag with n = 1), against a plain step."""
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record(dom.stream)
+        for _ in range(reps):
+            fn()
+        b.record(dom.stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    sep = timed(dom.diag)
+    fused = timed(lambda: dom.step_diag(1))
+    return {"plain_step_ms": round(ms_step, 4), "separate_diag_ms": round(sep, 4),
+            "step_with_diag_ms": round(fused, 4),
+            "in_step_extra_ms": round(fused - ms_step, 4)}
+
+
 def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32"):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
@@ -342,24 +363,36 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     t0 = time.perf_counter()
+    ev[0].record(dom.stream)
     dom.init_fields_device(fields, src_on_device=False)
+    ev[1].record(dom.stream)
     series = []
     done = 0
     while done < args.steps:
         k = min(diag_every, args.steps - done)
-        dom.step(k)
+        # the first of these k steps also returns the diagnostics of the state it reads
+        series.append(dom.step_diag(k))
         done += k
-        if done % diag_every == 0 or done == args.steps:
-            series.append(dom.diag())
+    ev[2].record(dom.stream)
     dom.moments_into(out, which=lbm.MOM_PRIM, on_device=False)
+    ev[3].record(dom.stream)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    phases = {"init_from_host_ms": round(ev[0].elapsed_time(ev[1]), 2),
+              "steps_with_diagnostics_ms": round(ev[1].elapsed_time(ev[2]), 2),
+              "moments_to_host_ms": round(ev[2].elapsed_time(ev[3]), 2)}
     e2e = {"value": round(job_value(world, ncell, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(fields.numel() * 4 / args.steps),
            "d2h_bytes_per_step": int((out.numel() * 4 + len(series) * 15 * 8) / args.steps),
-           "api": "lbm_init_fields(host) + lbm_step + lbm_diag every 50 steps + lbm_moments(host)",
-           "ek_final": series[-1]["ek_mean"] if series else None}
+           "api": "lbm_init_fields(host) + lbm_step_diag every 50 steps (FP64 diagnostics "
+                  "computed in the step) + lbm_moments(host)",
+           "diagnostics": len(series), "phases_gpu_ms": phases,
+           "ek_last": series[-1]["ek_mean"] if series else None}
+    diag_cost = None
+    if not args.no_variants and rank == 0:
+        diag_cost = diag_costs(torch, dom, ms_step)
     dom.close()
     del dom, fields, out
     torch.cuda.empty_cache()
@@ -381,6 +414,7 @@ def run_gpu(args):
                             "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4),
                             "steps": k2, "stated_err": stated_error(st)}
         variants[args.store] = {"stated_err": stated_error(args.store), "tune": tune}
+        variants["diagnostics"] = diag_cost
         variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
         variants["batch64_f16"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup,
                                             store="f16")

@@ -231,6 +231,21 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype);
  * found (returned by this call as well, after *out is filled). */
 lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out);
 
+/* Advances n >= 1 time steps like lbm_step, and the first of them also computes
+ * the diagnostics of the state it starts from (Sec. 3.2, Eq. 7; the values lbm_diag
+ * would return just before this call, with the same per-cell arithmetic) inside the
+ * step kernel, from the registers that hold the cell's moments, instead of a
+ * separate pass over the populations. Besides the populations, that step writes u
+ * and mu_local (16 bytes per cell) and one record per warp (13 doubles per 32 cells);
+ * a short reduction follows. Allocates the same scratch as lbm_diag plus the
+ * records on first use. Blocks the calling thread until the diagnostics are in
+ * *out (host); the other n - 1 steps stay queued, asynchronous, as with lbm_step.
+ * Sums may differ from lbm_diag's in the last bits (another summation order);
+ * extrema, counts and the dissipation integrals are identical. Errors as lbm_step;
+ * also returns LBM_E_NONFINITE (after filling *out) when the state had non-finite
+ * moments, and latches it. */
+lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out);
+
 /* lbm_diag without any memory allocation (no counterpart in the paper; a service
  * for callers that cannot allocate device memory when they sample diagnostics,
  * for example because a memory pool already holds the free device memory or
@@ -277,6 +292,24 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
  * (variant 0 or 1, see lbm_info_t) instead of the defaults or the autotuner's choice.
  * All configurations compute bit-identical populations. */
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
+
+/* ---- z-slab decomposition ------------------------------------------------------ */
+
+/* One domain split into z-slabs, one handle per slab (no counterpart in the paper,
+ * which runs one domain). Each slab handle is periodic in z on its own; D3Q7 moves
+ * populations only along the axes, so neighbouring slabs couple through the two
+ * z-moving populations of their boundary planes alone. These two calls move the raw
+ * stored values (element bits, no decoding) of storage slot `slot` (0 rest, 1 +x,
+ * 2 -x, 3 +y, 4 -y, 5 +z, 6 -z) of all 14 fields on plane z, as [k][y][x]: 14 * nx * ny
+ * elements of 4 bytes (F32) or 2 bytes (F16, BF16), to or from `buf` on the host or
+ * the device. Slots are those of the AA layout (after an even number of steps slot i
+ * of cell x holds f_i(x)). paper_2608_13437_gb300/slab.py holds the exchanges, before
+ * and after each odd step, that make a ring of slab handles step exactly like the
+ * whole domain; the handles must share Q_ref and the storage scales. Asynchronous on
+ * the handle's stream for device buffers, synchronous for host buffers.
+ * LBM_E_INVAL for z outside [0, nz), slot outside [0, 7) or a NULL buffer. */
+lbm_status lbm_plane_get(lbm_handle* h, int z, int slot, void* dst, int dst_on_device);
+lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int src_on_device);
 
 /* ---- many independent domains (batched mode) -------------------------------------
  * n periodic domains with their own sizes and parameters (one storage type for all,

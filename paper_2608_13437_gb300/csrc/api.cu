@@ -117,6 +117,18 @@ cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, 
   }
 }
 
+cudaError_t launch_step_diag(const DomainConst& P, int store, int parity, void* pop,
+                             const float* ghost, unsigned* flag, float* ufield, float* rec,
+                             int block_x, cudaStream_t s) {
+  switch (store) {
+    case LBM_STORE_F32:
+      return launch_step_diag_f32(P, parity, pop, ghost, flag, ufield, rec, block_x, s);
+    case LBM_STORE_F16:
+      return launch_step_diag_f16(P, parity, pop, ghost, flag, ufield, rec, block_x, s);
+    default: return launch_step_diag_bf16(P, parity, pop, ghost, flag, ufield, rec, block_x, s);
+  }
+}
+
 }  // namespace lbm
 
 struct lbm_handle {
@@ -145,6 +157,10 @@ struct lbm_handle {
   float* ufield = nullptr;     // diagnostics scratch: 4 floats per cell
   double* partials = nullptr;
   double* dout = nullptr;
+  float* wrec = nullptr;       // per-warp records of the diagnostic step
+  long long wrec_n = 0;
+  double* hdiag = nullptr;     // pinned host copy of dout and the flag
+  cudaEvent_t ev_diag = nullptr;
 };
 
 namespace {
@@ -353,6 +369,9 @@ lbm_status lbm_destroy(lbm_handle* h) {
   if (h->ufield) cudaFree(h->ufield);
   if (h->partials) cudaFree(h->partials);
   if (h->dout) cudaFree(h->dout);
+  if (h->wrec) cudaFree(h->wrec);
+  if (h->hdiag) cudaFreeHost(h->hdiag);
+  if (h->ev_diag) cudaEventDestroy(h->ev_diag);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
   return LBM_OK;
@@ -378,6 +397,7 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out) {
 }
 
 lbm_status lbm_init_tgv(lbm_handle* h, double U0, double M0, double rho0) {
+  Range range_("lbm_init_tgv");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
   if (!(std::isfinite(U0) && finite_pos(M0) && finite_pos(rho0)))
     return fail(LBM_E_INVAL, "TGV needs finite U0 and M0, rho0 > 0");
@@ -395,6 +415,7 @@ lbm_status lbm_init_tgv(lbm_handle* h, double U0, double M0, double rho0) {
 
 lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double left[3],
                             const double right[3]) {
+  Range range_("lbm_init_riemann");
   if (!h || !left || !right) return fail(LBM_E_INVAL, "NULL argument");
   if (axis < 0 || axis > 2) return fail(LBM_E_INVAL, "axis must be 0, 1 or 2");
   for (int j = 0; j < 3; ++j)
@@ -416,6 +437,7 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
 
 static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype,
                                    int kind, int nfield) {
+  Range range_("lbm_init_fields");
   if (!h || !fields) return fail(LBM_E_INVAL, "NULL argument");
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
   const size_t bytes = (size_t)nfield * h->ncell * (dtype == LBM_DT_F64 ? 8 : 4);
@@ -466,6 +488,7 @@ lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int d
 }
 
 lbm_status lbm_step(lbm_handle* h, int n) {
+  Range range_("lbm_step");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step before an init");
@@ -510,6 +533,7 @@ lbm_status lbm_synchronize(lbm_handle* h) {
 }
 
 lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, int dtype) {
+  Range range_("lbm_moments");
   if (!h || !dst) return fail(LBM_E_INVAL, "NULL argument");
   if (which != LBM_MOM_Q && which != LBM_MOM_PRIM) return fail(LBM_E_INVAL, "bad moment set");
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
@@ -533,9 +557,10 @@ lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, i
     const long long cnt = (c0 + chunk <= h->ncell) ? chunk : h->ncell - c0;
     e = launch_moments(h->P, h->prm.store, parity, h->pop, h->ghost, which, tmp,
                        dtype == LBM_DT_F64, c0, cnt, h->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(static_cast<char*>(dst) + c0 * es, (size_t)h->ncell * es, tmp,
-                            (size_t)cnt * es, (size_t)cnt * es, nf, cudaMemcpyDeviceToHost, h->stream);
+    for (int j = 0; j < nf && e == cudaSuccess; ++j)  // one plain copy per field row
+      e = cudaMemcpyAsync(static_cast<char*>(dst) + ((size_t)j * h->ncell + c0) * es,
+                          static_cast<char*>(tmp) + (size_t)j * cnt * es, (size_t)cnt * es,
+                          cudaMemcpyDeviceToHost, h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
@@ -565,9 +590,10 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
     const long long cnt = (c0 + chunk <= h->ncell) ? chunk : h->ncell - c0;
     e = launch_sensor(h->P, h->prm.store, parity, h->pop, h->ghost, tmp, dtype == LBM_DT_F64, c0, cnt,
                       h->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(static_cast<char*>(dst) + c0 * es, (size_t)h->ncell * es, tmp,
-                            (size_t)cnt * es, (size_t)cnt * es, 3, cudaMemcpyDeviceToHost, h->stream);
+    for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+      e = cudaMemcpyAsync(static_cast<char*>(dst) + ((size_t)j * h->ncell + c0) * es,
+                          static_cast<char*>(tmp) + (size_t)j * cnt * es, (size_t)cnt * es,
+                          cudaMemcpyDeviceToHost, h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
@@ -575,31 +601,28 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
   return LBM_OK;
 }
 
-lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
-  if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
-  if (!h->ufield) {
-    if (cudaMalloc(&h->ufield, sizeof(float) * 4 * (size_t)h->ncell) != cudaSuccess ||
-        cudaMalloc(&h->partials, sizeof(double) * (size_t)kDiagBlocks * (kDiagA + 2)) != cudaSuccess ||
-        cudaMalloc(&h->dout, sizeof(double) * 16) != cudaSuccess) {
-      cudaGetLastError();
-      if (h->ufield) cudaFree(h->ufield);
-      if (h->partials) cudaFree(h->partials);
-      if (h->dout) cudaFree(h->dout);
-      h->ufield = nullptr;
-      h->partials = h->dout = nullptr;
-      return fail(LBM_E_NOMEM, "diagnostic scratch allocation failed");
-    }
+static lbm_status ensure_diag_scratch(lbm_handle* h) {
+  if (h->ufield) return LBM_OK;
+  if (cudaMalloc(&h->ufield, sizeof(float) * 4 * (size_t)h->ncell) != cudaSuccess ||
+      cudaMalloc(&h->partials, sizeof(double) * (size_t)kDiagBlocks * (kDiagA + 2)) != cudaSuccess ||
+      cudaMalloc(&h->dout, sizeof(double) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->ufield) cudaFree(h->ufield);
+    if (h->partials) cudaFree(h->partials);
+    if (h->dout) cudaFree(h->dout);
+    h->ufield = nullptr;
+    h->partials = h->dout = nullptr;
+    return fail(LBM_E_NOMEM, "diagnostic scratch allocation failed");
   }
-  double r[16] = {0};
-  LBM_CUDA(launch_diag(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->ghost, h->ufield,
-                       h->partials, h->dout, h->stream));
-  LBM_CUDA(cudaMemcpyAsync(r, h->dout, sizeof(double) * (kDiagA + 2), cudaMemcpyDeviceToHost, h->stream));
-  unsigned flag = 0;
-  LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
-  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+// Fills *out from the reduced values r[0..kDiagA+2) of the state after `step` steps.
+static lbm_status finish_diag(lbm_handle* h, const double* r, bool flag, long long step,
+                              lbm_diag_t* out) {
   const double n = (double)h->ncell;
-  out->step = (double)h->step;
-  out->time = (double)h->step * h->dt;
+  out->step = (double)step;
+  out->time = (double)step * h->dt;
   out->sum_rho = r[0];
   out->sum_mx = r[1];
   out->sum_my = r[2];
@@ -616,6 +639,70 @@ lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
   if (flag || r[6] > 0) h->nonfinite = true;
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
+  Range range_("lbm_diag");
+  if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
+  lbm_status st = ensure_diag_scratch(h);
+  if (st != LBM_OK) return st;
+  double r[16] = {0};
+  LBM_CUDA(launch_diag(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->ghost, h->ufield,
+                       h->partials, h->dout, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(r, h->dout, sizeof(double) * (kDiagA + 2), cudaMemcpyDeviceToHost, h->stream));
+  unsigned flag = 0;
+  LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return finish_diag(h, r, flag != 0, h->step, out);
+}
+
+lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
+  Range range_("lbm_step_diag");
+  if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
+  if (n < 1) return fail(LBM_E_INVAL, "n must be >= 1");
+  if (!h->initialized) return fail(LBM_E_STATE, "lbm_step_diag before an init");
+  if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
+  lbm_status st = ensure_diag_scratch(h);
+  if (st != LBM_OK) return st;
+  const int bx = effective_block(h);
+  const long long nrec = step_diag_record_count(h->P, bx);
+  if (nrec > h->wrec_n) {
+    if (h->wrec) cudaFree(h->wrec);
+    h->wrec = nullptr;
+    h->wrec_n = 0;
+    if (cudaMalloc(&h->wrec, sizeof(float) * kDiagRecFloats * (size_t)nrec) != cudaSuccess) {
+      cudaGetLastError();
+      h->wrec = nullptr;
+      return fail(LBM_E_NOMEM, "diagnostic record allocation failed");
+    }
+    h->wrec_n = nrec;
+  }
+  if (!h->hdiag) {
+    if (cudaMallocHost(&h->hdiag, sizeof(double) * 17) != cudaSuccess) {
+      cudaGetLastError();
+      h->hdiag = nullptr;
+      return fail(LBM_E_NOMEM, "pinned host allocation failed");
+    }
+  }
+  if (!h->ev_diag) LBM_CUDA(cudaEventCreateWithFlags(&h->ev_diag, cudaEventDisableTiming));
+  const long long step0 = h->step;
+  LBM_CUDA(launch_step_diag(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->ghost, h->flag,
+                            h->ufield, h->wrec, bx, h->stream));
+  h->step += 1;
+  LBM_CUDA(launch_diag_records(h->P, h->wrec, nrec, h->ufield, h->partials, h->dout, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->hdiag, h->dout, sizeof(double) * (kDiagA + 2), cudaMemcpyDeviceToHost,
+                           h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->hdiag + 16, h->flag, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           h->stream));
+  LBM_CUDA(cudaEventRecord(h->ev_diag, h->stream));
+  if (n > 1) {
+    st = lbm_step(h, n - 1);
+    if (st != LBM_OK) return st;
+  }
+  LBM_CUDA(cudaEventSynchronize(h->ev_diag));
+  unsigned flag = 0;
+  std::memcpy(&flag, h->hdiag + 16, sizeof(flag));
+  return finish_diag(h, h->hdiag, flag != 0, step0, out);
 }
 
 static lbm_status pop_transfer(lbm_handle* h, void* buf, int on_device, int dtype, bool get) {
@@ -663,7 +750,42 @@ lbm_status lbm_populations_set(lbm_handle* h, const void* src, int src_on_device
   return LBM_OK;
 }
 
+static lbm_status plane_transfer(lbm_handle* h, int z, int slot, void* buf, int on_device, bool set) {
+  Range range_("lbm_plane");
+  if (!h || !buf) return fail(LBM_E_INVAL, "NULL argument");
+  if (z < 0 || z >= h->prm.nz) return fail(LBM_E_INVAL, "plane z = %d outside [0, %d)", z, h->prm.nz);
+  if (slot < 0 || slot >= kQ) return fail(LBM_E_INVAL, "slot %d outside [0, 7)", slot);
+  const size_t bytes = elem_size(h->prm.store) * kF * (size_t)h->prm.nx * h->prm.ny;
+  void* dev = buf;
+  if (!on_device) {
+    if (cudaMalloc(&dev, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_E_NOMEM, "staging allocation failed");
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (set && !on_device) e = cudaMemcpyAsync(dev, buf, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_plane(h->P, h->prm.store, h->pop, z, slot, dev, set ? 1 : 0, h->stream);
+  if (e == cudaSuccess && !set && !on_device)
+    e = cudaMemcpyAsync(buf, dev, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (!on_device) {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dev);
+  }
+  if (e != cudaSuccess) return fail(LBM_E_CUDA, "plane transfer failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status lbm_plane_get(lbm_handle* h, int z, int slot, void* dst, int dst_on_device) {
+  return plane_transfer(h, z, slot, dst, dst_on_device, false);
+}
+
+lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int src_on_device) {
+  return plane_transfer(h, z, slot, const_cast<void*>(src), src_on_device, true);
+}
+
 lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
+  Range range_("lbm_autotune");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
   if (!h->initialized) return fail(LBM_E_STATE, "autotune needs an initialised state");
   if (pairs_per_trial < 1) pairs_per_trial = 4;

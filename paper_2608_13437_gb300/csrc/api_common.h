@@ -1,12 +1,23 @@
 // Helpers shared by the C-ABI translation units (single domains and batches).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "lbm.h"
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// An NVTX range around an entry point (header-only NVTX v3: without a tool attached a
+// push/pop costs a few nanoseconds), so profiler timelines show the library's phases.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 extern thread_local std::string g_last_error;
 lbm_status fail(lbm_status s, const char* fmt, ...);

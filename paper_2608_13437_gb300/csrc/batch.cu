@@ -376,6 +376,7 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int n) {
+  Range range_("lbm_batch_step");
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!b->initialized) return fail(LBM_E_STATE, "lbm_batch_step before an init");
@@ -400,6 +401,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
 }
 
 lbm_status lbm_batch_step_sequential(lbm_batch* b, int n) {
+  Range range_("lbm_batch_step_sequential");
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!b->initialized) return fail(LBM_E_STATE, "lbm_batch_step_sequential before an init");

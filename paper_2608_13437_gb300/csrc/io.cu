@@ -129,6 +129,22 @@ __global__ void k_pop_set(const DomainConst P, int parity, S* __restrict__ pop, 
   }
 }
 
+// Raw stored values of storage slot `slot` of all fields on plane z, [k][y][x]; T is an
+// unsigned integer of the element's size, so the bits move unchanged.
+template <typename T>
+__global__ void k_plane(const DomainConst P, T* __restrict__ pop, int z, int slot,
+                        T* __restrict__ buf, int set) {
+  const long long plane = (long long)P.nx * P.ny;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < plane * kF;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(r / plane);
+    const long long cell = r - k * plane + plane * z;
+    const long long at = pop_index(cell, k, slot);
+    if (set) pop[at] = buf[r];
+    else buf[r] = pop[at];
+  }
+}
+
 int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -181,6 +197,17 @@ cudaError_t launch_pop_set(const DomainConst& P, int store, int parity, void* po
     case 1: k_pop_set<__half><<<grid, block, 0, s>>>(P, parity, (__half*)pop, k, i, in, dtype); break;
     default: k_pop_set<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (__nv_bfloat16*)pop, k, i, in, dtype); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane(const DomainConst& P, int store, void* pop, int z, int slot, void* buf,
+                         int set, cudaStream_t s) {
+  const int block = 256, grid = grid_for((long long)P.nx * P.ny * kF, block);
+  if (store == 0)
+    k_plane<unsigned><<<grid, block, 0, s>>>(P, (unsigned*)pop, z, slot, (unsigned*)buf, set);
+  else
+    k_plane<unsigned short><<<grid, block, 0, s>>>(P, (unsigned short*)pop, z, slot,
+                                                   (unsigned short*)buf, set);
   return cudaGetLastError();
 }
 

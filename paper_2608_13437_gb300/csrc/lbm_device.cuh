@@ -397,12 +397,22 @@ struct SensorOut {
   float omega_h;
 };
 
+// The cell's own FP32 moments and closure as the step computes them, for the
+// diagnostics (Sec. 3.2).
+struct CellDiag {
+  float D[5];      // zeroth-moment deviations of rho, rho u, E from the reference
+  float rho, T, mu_T;
+  float u[3], m[3];
+  bool finite;     // all 14 zeroth moments finite
+};
+
 // Collides one cell in place on its decoded deviations d[k][i]. Returns the sum of
 // the zeroth-moment deviations (a finiteness probe). With kSensor the sensor
-// values are reported and the populations are left unchanged.
-template <bool kSensor>
+// values are reported and the populations are left unchanged. With kDiag the
+// moments and closure are also copied to *cd.
+template <bool kSensor, bool kDiag = false>
 __device__ __forceinline__ float collide_cell(const DomainConst& P, float (&d)[kF][kQ],
-                                              SensorOut* so) {
+                                              SensorOut* so, CellDiag* cd = nullptr) {
   // Zeroth moments (Sec. 2.2: Q from the zeroth moment alone), i ascending.
   float D[kF];
 #pragma unroll
@@ -419,6 +429,22 @@ __device__ __forceinline__ float collide_cell(const DomainConst& P, float (&d)[k
   Q[4] = add(Q[4], P.E_ref);
   Prim<float> s;
   closure<float>(Q, P.gm1, P.mu, P.visc0, P.heat0, P.inv_T_ref, P.sutherland, s);
+  if constexpr (kDiag) {
+    bool fin = true;
+#pragma unroll
+    for (int k = 0; k < kF; ++k) fin = fin && isfinite(D[k]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) cd->D[k] = D[k];
+    cd->rho = s.rho;
+    cd->T = s.T;
+    cd->mu_T = s.mu_T;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cd->u[a] = s.u[a];
+      cd->m[a] = s.m[a];
+    }
+    cd->finite = fin;
+  }
 
   // Eq. 6: tau_base = 1/2 + 4 f_mu (mu_T/rho) dt/dx^2, omega = 1/tau_base.
   const float tau_b = fma_(mul(P.fmu_coef, s.mu_T), s.inv_rho, 0.5f);

@@ -28,6 +28,23 @@ cudaError_t launch_step_f16(const DomainConst& P, int parity, void* pop, const f
 cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const float* ghost,
                              unsigned* flag, int block_x, int variant, cudaStream_t s);
 
+// The same step that also computes the diagnostics of the state it reads (step_diag_*.cu):
+// writes u and mu_local to ufield (4 floats per cell) and one record of 17 floats per
+// warp to rec (step_diag_record_count of them; block_x as for launch_step_*).
+cudaError_t launch_step_diag_f32(const DomainConst& P, int parity, void* pop, const float* ghost,
+                                 unsigned* flag, float* ufield, float* rec, int block_x,
+                                 cudaStream_t s);
+cudaError_t launch_step_diag_f16(const DomainConst& P, int parity, void* pop, const float* ghost,
+                                 unsigned* flag, float* ufield, float* rec, int block_x,
+                                 cudaStream_t s);
+cudaError_t launch_step_diag_bf16(const DomainConst& P, int parity, void* pop, const float* ghost,
+                                  unsigned* flag, float* ufield, float* rec, int block_x,
+                                  cudaStream_t s);
+constexpr int kDiagRecFloats = 17;  // words of one warp record
+inline long long step_diag_record_count(const DomainConst& P, int block_x) {
+  return (long long)((P.nx + block_x - 1) / block_x) * P.ny * P.nz * (block_x / 32);
+}
+
 // Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields (rho, u, p),
 // 3 caller zeroth moments (14 fields).
 struct InitSpec {
@@ -61,6 +78,10 @@ cudaError_t launch_pop_get(const DomainConst& P, int store, int parity, const vo
                            const float* ghost, int k, int i, void* out, int dtype, cudaStream_t s);
 cudaError_t launch_pop_set(const DomainConst& P, int store, int parity, void* pop, int k, int i,
                            const void* in, int dtype, cudaStream_t s);
+// Raw stored values of storage slot `slot` on plane z, all fields, [k][y][x] in the
+// storage's element size: copied into buf (set = 0) or from buf (set = 1).
+cudaError_t launch_plane(const DomainConst& P, int store, void* pop, int z, int slot, void* buf,
+                         int set, cudaStream_t s);
 
 // Diagnostics (diag.cu).
 constexpr int kDiagA = 13;  // sums: rho mx my mz E ke nonfinite | max: mach cfl | min: rho T
@@ -69,5 +90,10 @@ constexpr int kDiagBlocks = 1216;
 cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void* pop,
                         const float* ghost, float* ufield, double* partials, double* out16,
                         cudaStream_t s);
+// Finishes the diagnostics from the records of launch_step_diag_* (nrec of them) and
+// the u field it wrote; same partials and output as launch_diag.
+cudaError_t launch_diag_records(const DomainConst& P, const float* rec, long long nrec,
+                                const float* ufield, double* partials, double* out16,
+                                cudaStream_t s);
 
 }  // namespace lbm

@@ -1,0 +1,70 @@
+// The fused step with the diagnostics of the state it reads (Sec. 3.2, Eq. 7): the
+// same cell update as k_step, and from the same registers, one diagnostic record per
+// warp (sums, extrema, non-finite count of its 32 cells) plus u and mu_local into a
+// 4-float-per-cell field for the velocity-gradient pass. No separate pass over the
+// populations is needed.
+#pragma once
+
+#include "diag_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static_assert(kDiagRecFloats == kDiagRecWords, "warp record size");
+
+template <int PARITY, typename S, bool HELD>
+__global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __restrict__ pop,
+                                                      const float* __restrict__ ghost,
+                                                      unsigned* __restrict__ flag,
+                                                      float* __restrict__ ufield,
+                                                      float* __restrict__ rec) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  DiagAcc acc;
+  diag_zero(acc);
+  if (x < P.nx) {  // no early return: every lane takes part in the warp reduction
+    const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
+    float d[kF][kQ];
+    load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
+    CellDiag cd;
+    if (P.collide) {
+      const float probe = collide_cell<false, true>(P, d, nullptr, &cd);
+      if (!isfinite(probe)) atomicOr(flag, 1u);
+    } else {
+      SensorOut so;
+      collide_cell<true, true>(P, d, &so, &cd);
+    }
+    store_cell<PARITY, S>(P, pop, c, d);
+    diag_add_cell(P, cd, acc);
+    const long long n = P.ncell;
+    const long long cell = x + (long long)P.nx * (blockIdx.y + (long long)P.ny * blockIdx.z);
+    ufield[cell] = cd.u[0];
+    ufield[n + cell] = cd.u[1];
+    ufield[2 * n + cell] = cd.u[2];
+    ufield[3 * n + cell] = cd.mu_T;
+  }
+  diag_warp_reduce(acc);
+  if ((threadIdx.x & 31) == 0) {
+    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    diag_store_words(acc, rec + (blk * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDiagRecWords);
+  }
+}
+
+template <typename S>
+cudaError_t launch_step_diag_t(const DomainConst& P, int parity, void* pop, const float* ghost,
+                               unsigned* flag, float* ufield, float* rec, int block_x,
+                               cudaStream_t s) {
+  if (block_x < 32 || block_x > 128 || (block_x & 31)) return cudaErrorInvalidConfiguration;
+  const dim3 block(block_x);
+  const dim3 grid((P.nx + block_x - 1) / block_x, P.ny, P.nz);
+  S* p = static_cast<S*>(pop);
+  if (P.bc_x) {
+    if (parity) k_step_diag<1, S, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  } else {
+    if (parity) k_step_diag<1, S, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

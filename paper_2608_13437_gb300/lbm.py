@@ -89,6 +89,9 @@ _SIGNATURES = {
     "lbm_sensor": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_diag": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
     "lbm_diag_static": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
+    "lbm_step_diag": (_IP, [_VP, _IP, ctypes.POINTER(LbmDiag)]),
+    "lbm_plane_get": (_IP, [_VP, _IP, _IP, _VP, _IP]),
+    "lbm_plane_set": (_IP, [_VP, _IP, _IP, _VP, _IP]),
     "lbm_populations_get": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_populations_set": (_IP, [_VP, _VP, _IP, _IP]),
     "lbm_save": (_IP, [_VP, ctypes.c_char_p]),
@@ -235,6 +238,17 @@ class Domain:
     def step(self, n=1):
         check(lib().lbm_step(self._h, int(n)))
 
+    def step_diag(self, n=1) -> dict:
+        """n steps; the first also returns the diagnostics of the state it starts from
+        (computed inside the step kernel). Same keys as diag()."""
+        d = LbmDiag()
+        st = lib().lbm_step_diag(self._h, int(n), ctypes.byref(d))
+        res = {k: getattr(d, k) for k in DIAG_FIELDS}
+        if st not in (LBM_OK, LBM_E_NONFINITE):
+            check(st)
+        res["status"] = st
+        return res
+
     def synchronize(self):
         check(lib().lbm_synchronize(self._h))
 
@@ -296,6 +310,34 @@ class Domain:
         else:
             f = np.ascontiguousarray(f, dtype=np.float64)
             check(lib().lbm_populations_set(self._h, _np_ptr(f), 0, DT_F64))
+
+    def plane_get(self, z: int, slot: int, out=None):
+        """Raw stored values of storage slot `slot` on plane z, (14, ny, nx): a device
+        tensor (int32 for F32 storage, int16 otherwise) unless `out` is a numpy array."""
+        if isinstance(out, np.ndarray):
+            check(lib().lbm_plane_get(self._h, int(z), int(slot), _np_ptr(out), 0))
+            return out
+        if out is None:
+            out = self.torch.empty((14, self.ny, self.nx), dtype=self.plane_dtype(), device=self.device)
+        check(lib().lbm_plane_get(self._h, int(z), int(slot), ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def plane_set(self, z: int, slot: int, buf):
+        if isinstance(buf, np.ndarray):
+            buf = np.ascontiguousarray(buf)
+            check(lib().lbm_plane_set(self._h, int(z), int(slot), _np_ptr(buf), 0))
+        else:
+            buf = buf.contiguous()
+            check(lib().lbm_plane_set(self._h, int(z), int(slot), ctypes.c_void_p(buf.data_ptr()), 1))
+
+    def plane_dtype(self, numpy=False):
+        if numpy:
+            return np.int32 if self.store == STORE_F32 else np.int16
+        return self.torch.int32 if self.store == STORE_F32 else self.torch.int16
+
+    @property
+    def step_count(self) -> int:
+        return int(self.info()["step"])
 
     def save(self, path: str):
         check(lib().lbm_save(self._h, path.encode()))

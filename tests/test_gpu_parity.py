@@ -247,6 +247,91 @@ def test_diag_matches_oracle(lbm, oracle_mod):
     dom.close()
 
 
+EXACT_DIAG = ("max_mach", "max_cfl", "min_rho", "min_T", "nonfinite", "eps_s_raw", "eps_d_raw",
+              "step", "time")
+
+
+def _step_diag_case(lbm, case):
+    if case == "tgv32_f32":
+        p, store = inputs.tgv_params(32), "f32"
+    elif case == "ragged_f16":
+        p = inputs.tgv_params(16)
+        p.update(nx=40, ny=12, nz=9, dx=2 * np.pi / 40, sutherland=0, f_mu=0.3, J_min=1e-3,
+                 tau_R=0.05, tau_q=0.05)
+        store = "f16"
+    else:
+        p, store = inputs.sod_params(256), "bf16"
+    dom = lbm.Domain(p, store=store)
+    if case == "tgv32_f32":
+        dom.init_tgv(1.0, 1.25, 1.0)
+    elif case == "ragged_f16":
+        s = inputs.random_smooth_state(40, 12, 9, seed=31, amp=0.15)
+        dom.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"])
+    else:
+        dom.init_riemann(0, 128, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    return dom
+
+
+@pytest.mark.parametrize("case,block", [("tgv32_f32", 64), ("ragged_f16", 64), ("ragged_f16", 32),
+                                        ("sod_held_bf16", 128)])
+def test_step_diag_matches_separate_pass(lbm, case, block):
+    """lbm_step_diag computes, inside its first step, the diagnostics lbm_diag gives for
+    the state before that step: extrema, counts and the dissipation integrals bit for
+    bit, sums to 1e-11 (float-float sums, about 48 bits, grouped differently); the
+    populations after n steps equal those of lbm_step bit for bit. Covers a partial
+    warp (nx = 40), both parities and held x ends."""
+    a, b = _step_diag_case(lbm, case), _step_diag_case(lbm, case)
+    for d in (a, b):
+        d.set_kernel_config(block, 0)
+        d.step(3)  # odd parity at the diagnostic step
+    ref = a.diag()
+    a.step(6)
+    got = b.step_diag(6)
+    assert got["status"] == lbm.LBM_OK and ref["status"] == lbm.LBM_OK
+    for k in EXACT_DIAG:
+        assert got[k] == ref[k], k
+    for k in ("sum_rho", "sum_E", "ek_mean"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-11), k
+    for k in ("sum_mx", "sum_my", "sum_mz"):
+        assert abs(got[k] - ref[k]) <= 1e-11 * ref["sum_rho"], k
+    assert got["step"] == 3
+    assert np.array_equal(a.populations("native"), b.populations("native"))
+    # the next diagnostic of b is that of the state after all 9 steps
+    nxt = b.step_diag(1)
+    assert nxt["step"] == 9 and nxt["eps_s_raw"] == a.diag()["eps_s_raw"]
+    a.close()
+    b.close()
+
+
+def test_step_diag_matches_oracle_on_tgv(lbm, oracle_mod):
+    """The in-step diagnostics against the FP64 oracle's, at the tolerances of lbm_diag."""
+    dom, o = _tgv_pair(lbm, 32, 40)
+    g, r = dom.step_diag(2), o.diag()
+    for k in ("sum_rho", "sum_E", "ek_mean", "min_rho", "min_T", "max_mach", "max_cfl"):
+        assert g[k] == pytest.approx(r[k], rel=2e-6), k
+    for k in ("eps_s_raw", "eps_d_raw"):
+        assert g[k] == pytest.approx(r[k], rel=1e-4), k
+    assert g["nonfinite"] == 0 and g["step"] == 40
+    dom.close()
+
+
+def test_step_diag_reports_non_finite_state(lbm):
+    p = inputs.tgv_params(8)
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    f = dom.populations()
+    f[2, 1, 3, 2, 1] = np.inf
+    dom.set_populations(f)
+    d = dom.step_diag(1)
+    assert d["status"] == lbm.LBM_E_NONFINITE and d["nonfinite"] == 1
+    with pytest.raises(lbm.LbmError) as ei:
+        dom.step(1)
+    assert ei.value.status == lbm.LBM_E_NONFINITE
+    dom.init_tgv(1.0, 1.25, 1.0)
+    assert dom.step_diag(2)["status"] == lbm.LBM_OK
+    dom.close()
+
+
 def test_graphs_and_direct_launches_agree_bitwise(lbm):
     p = inputs.tgv_params(32)
     a = lbm.Domain(p, use_graphs=True)
