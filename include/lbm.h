@@ -115,8 +115,12 @@ typedef struct {
   size_t population_bytes;  /* bytes of the population buffer */
   int store;
   int block_x;              /* threads per block of the step kernel */
-  int variant;              /* register budget of the step kernel: 0 = 3 blocks of 128
-                               threads per SM (<= 170 registers), 1 = 4 blocks (<= 128) */
+  int variant;              /* form of the step kernel: 0 = plain loads, 3 blocks of 128
+                               threads per SM (<= 170 registers); 1 = plain loads, 4 blocks
+                               (<= 128 registers); 2, 3, 4 = reads staged through shared
+                               memory by bulk asynchronous copies, a persistent grid of
+                               4-warp blocks: 2 stages per warp with <= 170 registers (2),
+                               2 stages with <= 128 (3), 3 stages with <= 170 (4) */
 } lbm_info_t;
 
 /* Diagnostics (Sec. 3.2, Eq. 7). Sums and extrema in FP64 over all cells.
@@ -281,16 +285,22 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 
 /* ---- tuning ------------------------------------------------------------------- */
 
-/* Times the step kernel for each candidate block size and register budget (whole
- * step pairs, CUDA events on the handle's stream) and keeps the fastest in the
+/* Times the step kernel for each candidate form (variants 0 and 1 at blocks of 64
+ * and 128 threads; the staged variants 2-4 where the domain allows them) on whole
+ * step pairs with CUDA events on the handle's stream, and keeps the fastest in the
  * handle; returns it in *out if out != NULL. Needs an initialised state
  * (LBM_E_STATE otherwise); each candidate runs on the live state, so the state
  * advances by an even number of steps: re-init before the run you keep. */
 lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
 
-/* Fixes the step kernel's block size (32, 64, 96 or 128 threads) and register budget
- * (variant 0 or 1, see lbm_info_t) instead of the defaults or the autotuner's choice.
- * All configurations compute bit-identical populations. */
+/* Fixes the step kernel's form (variant 0-4, see lbm_info_t) and, for variants 0 and
+ * 1, its block size (32, 64, 96 or 128 threads; ignored by the staged variants)
+ * instead of the defaults or the autotuner's choice. The staged variants need a
+ * periodic x axis and nx a multiple of 32 (whole 32-cell tiles per row; LBM_E_INVAL
+ * otherwise). All forms compute bit-identical populations. A staged step whose wait
+ * for a copy runs out (bounded; it does not happen in normal operation) stops,
+ * reports LBM_E_CUDA from the next synchronising call and refuses further steps
+ * until a re-init. */
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
 
 /* ---- z-slab decomposition ------------------------------------------------------ */

@@ -117,6 +117,23 @@ cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, 
   }
 }
 
+cudaError_t staged_prepare(const DomainConst& P, int store, int variant, int* grid) {
+  switch (store) {
+    case LBM_STORE_F32: return staged_prepare_f32(P, variant, grid);
+    case LBM_STORE_F16: return staged_prepare_f16(P, variant, grid);
+    default: return staged_prepare_bf16(P, variant, grid);
+  }
+}
+
+cudaError_t launch_step_staged(const DomainConst& P, int store, int parity, void* pop, unsigned* flag,
+                               int variant, int grid, cudaStream_t s) {
+  switch (store) {
+    case LBM_STORE_F32: return launch_step_staged_f32(P, parity, pop, flag, variant, grid, s);
+    case LBM_STORE_F16: return launch_step_staged_f16(P, parity, pop, flag, variant, grid, s);
+    default: return launch_step_staged_bf16(P, parity, pop, flag, variant, grid, s);
+  }
+}
+
 cudaError_t launch_step_diag(const DomainConst& P, int store, int parity, void* pop,
                              const float* ghost, unsigned* flag, float* ufield, float* rec,
                              int block_x, cudaStream_t s) {
@@ -151,7 +168,9 @@ struct lbm_handle {
   bool initialized = false;
   bool nonfinite = false;
   int block_x = 64;
-  int variant = 0;             // register budget of the step kernel (see launch_step_t)
+  int variant = 0;             // step kernel: register budget (0, 1) or staged form (2-4)
+  int staged_grid = 0;         // persistent grid of the staged forms
+  bool stalled = false;        // a staged step gave up waiting for a bulk copy
   cudaGraphExec_t g_pair = nullptr, g_chunk = nullptr;
   bool graphs_valid = false;
   float* ufield = nullptr;     // diagnostics scratch: 4 floats per cell
@@ -160,6 +179,7 @@ struct lbm_handle {
   float* wrec = nullptr;       // per-warp records of the diagnostic step
   long long wrec_n = 0;
   double* hdiag = nullptr;     // pinned host copy of dout and the flag
+  void* stage = nullptr;       // device staging for host-side outputs (kStageBytes)
   cudaEvent_t ev_diag = nullptr;
 };
 
@@ -187,13 +207,27 @@ int effective_block(const lbm_handle* h) {
   return b > need ? need : b;
 }
 
+cudaError_t step_launch(lbm_handle* h, int parity, cudaStream_t s) {
+  if (h->variant >= kFirstStagedVariant)
+    return launch_step_staged(h->P, h->prm.store, parity, h->pop, h->flag, h->variant,
+                              h->staged_grid, s);
+  return launch_step(h->P, h->prm.store, parity, h->pop, h->ghost, h->flag, effective_block(h),
+                     h->variant, s);
+}
+
+// Flag bits written by the step kernels: 1 = a non-finite moment, 2 = a staged step
+// gave up waiting for a bulk copy (its state is then incomplete).
+void latch_flag(lbm_handle* h, unsigned flag) {
+  if (flag & 1u) h->nonfinite = true;
+  if (flag & 2u) h->stalled = true;
+}
+
 lbm_status capture(lbm_handle* h, int pairs, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int j = 0; j < 2 * pairs && le == cudaSuccess; ++j)
-    le = launch_step(h->P, h->prm.store, j & 1, h->pop, h->ghost, h->flag, effective_block(h),
-                     h->variant, h->cap);
+    le = step_launch(h, j & 1, h->cap);
   cudaError_t ee = cudaStreamEndCapture(h->cap, &g);
   if (le != cudaSuccess || ee != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -218,8 +252,7 @@ lbm_status ensure_graphs(lbm_handle* h) {
 }
 
 lbm_status direct_step(lbm_handle* h) {
-  LBM_CUDA(launch_step(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->ghost, h->flag,
-                       effective_block(h), h->variant, h->stream));
+  LBM_CUDA(step_launch(h, (int)(h->step & 1), h->stream));
   h->step += 1;
   return LBM_OK;
 }
@@ -271,6 +304,7 @@ lbm_status run_init(lbm_handle* h, InitSpec& sp) {
   h->step = 0;
   h->initialized = true;
   h->nonfinite = false;
+  h->stalled = false;
   h->graphs_valid = false;
   return LBM_OK;
 }
@@ -370,6 +404,7 @@ lbm_status lbm_destroy(lbm_handle* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->dout) cudaFree(h->dout);
   if (h->wrec) cudaFree(h->wrec);
+  if (h->stage) cudaFree(h->stage);
   if (h->hdiag) cudaFreeHost(h->hdiag);
   if (h->ev_diag) cudaEventDestroy(h->ev_diag);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -493,6 +528,7 @@ lbm_status lbm_step(lbm_handle* h, int n) {
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
+  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   if (n == 0) return LBM_OK;
   if (!h->prm.use_graphs) {
     for (int j = 0; j < n; ++j) {
@@ -527,8 +563,21 @@ lbm_status lbm_synchronize(lbm_handle* h) {
   unsigned flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
-  if (flag) h->nonfinite = true;
+  latch_flag(h, flag);
+  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments detected");
+  return LBM_OK;
+}
+
+// The handle's device staging buffer for outputs written to host memory, allocated on
+// first use and kept (no allocation or implicit device synchronisation per call).
+static lbm_status ensure_stage(lbm_handle* h) {
+  if (h->stage) return LBM_OK;
+  if (cudaMalloc(&h->stage, kStageBytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->stage = nullptr;
+    return fail(LBM_E_NOMEM, "staging allocation failed");
+  }
   return LBM_OK;
 }
 
@@ -547,11 +596,9 @@ lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, i
   }
   long long chunk = (long long)(kStageBytes / (es * nf));
   if (chunk > h->ncell) chunk = h->ncell;
-  void* tmp = nullptr;
-  if (cudaMalloc(&tmp, (size_t)chunk * nf * es) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(LBM_E_NOMEM, "staging allocation failed");
-  }
+  lbm_status st = ensure_stage(h);
+  if (st != LBM_OK) return st;
+  void* tmp = h->stage;
   cudaError_t e = cudaSuccess;
   for (long long c0 = 0; c0 < h->ncell && e == cudaSuccess; c0 += chunk) {
     const long long cnt = (c0 + chunk <= h->ncell) ? chunk : h->ncell - c0;
@@ -563,7 +610,6 @@ lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, i
                           cudaMemcpyDeviceToHost, h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(tmp);
   if (e != cudaSuccess) return fail(LBM_E_CUDA, "moments failed: %s", cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -580,11 +626,9 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
   }
   long long chunk = (long long)(kStageBytes / (es * 3));
   if (chunk > h->ncell) chunk = h->ncell;
-  void* tmp = nullptr;
-  if (cudaMalloc(&tmp, (size_t)chunk * 3 * es) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(LBM_E_NOMEM, "staging allocation failed");
-  }
+  lbm_status st = ensure_stage(h);
+  if (st != LBM_OK) return st;
+  void* tmp = h->stage;
   cudaError_t e = cudaSuccess;
   for (long long c0 = 0; c0 < h->ncell && e == cudaSuccess; c0 += chunk) {
     const long long cnt = (c0 + chunk <= h->ncell) ? chunk : h->ncell - c0;
@@ -596,7 +640,6 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
                           cudaMemcpyDeviceToHost, h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(tmp);
   if (e != cudaSuccess) return fail(LBM_E_CUDA, "sensor failed: %s", cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -618,7 +661,7 @@ static lbm_status ensure_diag_scratch(lbm_handle* h) {
 }
 
 // Fills *out from the reduced values r[0..kDiagA+2) of the state after `step` steps.
-static lbm_status finish_diag(lbm_handle* h, const double* r, bool flag, long long step,
+static lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, long long step,
                               lbm_diag_t* out) {
   const double n = (double)h->ncell;
   out->step = (double)step;
@@ -636,7 +679,9 @@ static lbm_status finish_diag(lbm_handle* h, const double* r, bool flag, long lo
   out->min_T = r[12];
   out->eps_s_raw = r[13] / n;
   out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
-  if (flag || r[6] > 0) h->nonfinite = true;
+  latch_flag(h, flag);
+  if (r[6] > 0) h->nonfinite = true;
+  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
 }
@@ -653,7 +698,7 @@ lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
   unsigned flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
-  return finish_diag(h, r, flag != 0, h->step, out);
+  return finish_diag(h, r, flag, h->step, out);
 }
 
 lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
@@ -662,6 +707,7 @@ lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
   if (n < 1) return fail(LBM_E_INVAL, "n must be >= 1");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step_diag before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
+  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   lbm_status st = ensure_diag_scratch(h);
   if (st != LBM_OK) return st;
   const int bx = effective_block(h);
@@ -702,7 +748,7 @@ lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
   LBM_CUDA(cudaEventSynchronize(h->ev_diag));
   unsigned flag = 0;
   std::memcpy(&flag, h->hdiag + 16, sizeof(flag));
-  return finish_diag(h, h->hdiag, flag != 0, step0, out);
+  return finish_diag(h, h->hdiag, flag, step0, out);
 }
 
 static lbm_status pop_transfer(lbm_handle* h, void* buf, int on_device, int dtype, bool get) {
@@ -788,47 +834,69 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   Range range_("lbm_autotune");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
   if (!h->initialized) return fail(LBM_E_STATE, "autotune needs an initialised state");
+  if (h->nonfinite || h->stalled) return fail(LBM_E_STATE, "autotune on a failed state; re-init");
   if (pairs_per_trial < 1) pairs_per_trial = 4;
-  const int blocks[] = {64, 128};
-  const int variants[] = {0, 1};
+  struct Cand {
+    int variant, block;
+  };
+  std::vector<Cand> cands;
+  for (int v : {0, 1})
+    for (int b : {64, 128})
+      if (b <= 32 * ((h->P.nx + 31) / 32) || b == 64) cands.push_back({v, b});
+  if (staged_eligible(h->P))
+    for (int v = kFirstStagedVariant; v <= kLastStagedVariant; ++v) cands.push_back({v, 128});
   cudaEvent_t a, b;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
-  int best_b = h->block_x, best_v = h->variant, tried = 0;
-  for (int cv : variants)
-    for (int cb : blocks) {
-      if (cb > 32 * ((h->P.nx + 31) / 32) && cb != blocks[0]) continue;
-      h->block_x = cb;
-      h->variant = cv;
-      for (int j = 0; j < 2; ++j)  // warm-up pair
-        LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
-                             effective_block(h), h->variant, h->stream));
-      h->step += 2;
-      LBM_CUDA(cudaEventRecord(a, h->stream));
-      for (int j = 0; j < 2 * pairs_per_trial; ++j)
-        LBM_CUDA(launch_step(h->P, h->prm.store, (int)((h->step + j) & 1), h->pop, h->ghost, h->flag,
-                             effective_block(h), h->variant, h->stream));
-      h->step += 2 * pairs_per_trial;
-      LBM_CUDA(cudaEventRecord(b, h->stream));
-      LBM_CUDA(cudaEventSynchronize(b));
-      float ms = 0;
-      LBM_CUDA(cudaEventElapsedTime(&ms, a, b));
-      ms /= (float)(2 * pairs_per_trial);
-      ++tried;
-      if (ms < best) {
-        best = ms;
-        best_b = cb;
-        best_v = cv;
+  int best_b = h->block_x, best_v = h->variant, best_grid = h->staged_grid, tried = 0;
+  cudaError_t err = cudaSuccess;
+  for (const Cand& c : cands) {
+    int grid = 0;
+    if (c.variant >= kFirstStagedVariant) {
+      if (staged_prepare(h->P, h->prm.store, c.variant, &grid) != cudaSuccess) {
+        cudaGetLastError();
+        continue;  // this form does not fit the device (shared memory); skip it
       }
     }
+    h->block_x = c.block;
+    h->variant = c.variant;
+    h->staged_grid = grid;
+    for (int j = 0; j < 2 && err == cudaSuccess; ++j)  // warm-up pair
+      err = step_launch(h, (int)((h->step + j) & 1), h->stream);
+    h->step += 2;
+    if (err == cudaSuccess) err = cudaEventRecord(a, h->stream);
+    for (int j = 0; j < 2 * pairs_per_trial && err == cudaSuccess; ++j)
+      err = step_launch(h, (int)((h->step + j) & 1), h->stream);
+    h->step += 2 * pairs_per_trial;
+    if (err == cudaSuccess) err = cudaEventRecord(b, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(b);
+    float ms = 0;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+    if (err != cudaSuccess) break;
+    ms /= (float)(2 * pairs_per_trial);
+    ++tried;
+    if (ms < best) {
+      best = ms;
+      best_b = c.block;
+      best_v = c.variant;
+      best_grid = grid;
+    }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->block_x = best_b;
   h->variant = best_v;
+  h->staged_grid = best_grid;
   h->graphs_valid = false;
+  if (err != cudaSuccess) return fail(LBM_E_CUDA, "autotune failed: %s", cudaGetErrorString(err));
+  unsigned flag = 0;
+  LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  latch_flag(h, flag);
+  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   if (out) {
-    out->block_x = effective_block(h);
+    out->block_x = best_v >= kFirstStagedVariant ? 128 : effective_block(h);
     out->variant = best_v;
     out->ms_per_step = best;
     out->candidates = tried;
@@ -838,9 +906,19 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
 
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  if (variant < 0 || variant > kLastStagedVariant) return fail(LBM_E_INVAL, "variant must be 0 to 4");
+  if (variant >= kFirstStagedVariant) {
+    if (!staged_eligible(h->P))
+      return fail(LBM_E_INVAL, "staged variants need periodic x and nx a multiple of 32");
+    int grid = 0;
+    LBM_CUDA(staged_prepare(h->P, h->prm.store, variant, &grid));
+    h->variant = variant;
+    h->staged_grid = grid;
+    h->graphs_valid = false;
+    return LBM_OK;
+  }
   if (block_x < 32 || block_x > 128 || (block_x & 31))
     return fail(LBM_E_INVAL, "block_x must be 32, 64, 96 or 128");
-  if (variant < 0 || variant > 1) return fail(LBM_E_INVAL, "variant must be 0 or 1");
   h->block_x = block_x;
   h->variant = variant;
   h->graphs_valid = false;
@@ -983,6 +1061,10 @@ HandleView handle_view(lbm_handle* h) {
 }
 
 void latch_nonfinite(lbm_handle* h) { h->nonfinite = true; }
+
+void latch_step_flag(lbm_handle* h, unsigned flag) { latch_flag(h, flag); }
+
+bool stall_latched(const lbm_handle* h) { return h->stalled; }
 
 bool nonfinite_latched(const lbm_handle* h) { return h->nonfinite; }
 

@@ -45,5 +45,7 @@ struct HandleView {
 HandleView handle_view(lbm_handle* h);
 void latch_nonfinite(lbm_handle* h);
 bool nonfinite_latched(const lbm_handle* h);
+void latch_step_flag(lbm_handle* h, unsigned flag);  // bit 0 non-finite, bit 1 stalled copy
+bool stall_latched(const lbm_handle* h);
 
 }  // namespace lbm

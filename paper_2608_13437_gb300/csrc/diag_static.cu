@@ -107,7 +107,9 @@ extern "C" lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out) {
   out->min_T = r[12];
   out->eps_s_raw = r[13] / n;
   out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
-  if (flag || r[6] > 0) latch_nonfinite(h);
+  latch_step_flag(h, flag);
+  if (r[6] > 0) latch_nonfinite(h);
+  if (stall_latched(h)) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
   if (nonfinite_latched(h)) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
 }

@@ -332,6 +332,53 @@ def test_step_diag_reports_non_finite_state(lbm):
     dom.close()
 
 
+@pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
+def test_staged_variants_agree_bitwise(lbm, store):
+    """The forms of the step that stage their reads through shared memory with bulk
+    asynchronous copies (variants 2-4) compute the plain kernel's populations bit for
+    bit: both parities (23 steps), rows of one to three tiles, y and z extents from 1
+    to 5 (periodic wraps onto the same tile included)."""
+    for nx, ny, nz in ((64, 5, 3), (32, 1, 4), (96, 3, 1)):
+        p = inputs.tgv_params(16)
+        p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / nx, sutherland=0, f_mu=0.3, J_min=1e-3,
+                 tau_R=0.05, tau_q=0.05)
+        s = inputs.random_smooth_state(nx, ny, nz, seed=41, amp=0.15)
+        ref = None
+        for var in (0, 2, 3, 4):
+            d = lbm.Domain(p, store=store)
+            d.set_kernel_config(64, var)
+            d.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"])
+            d.step(23)
+            d.synchronize()
+            f = d.populations("native")
+            bits = f.view(np.uint32) if f.dtype == np.float32 else f
+            assert d.info()["variant"] == var
+            d.close()
+            if ref is None:
+                ref = bits
+            else:
+                assert np.array_equal(bits, ref), (nx, ny, nz, var)
+
+
+def test_staged_variants_need_whole_tile_rows(lbm):
+    p = inputs.tgv_params(16)
+    p.update(nx=40, ny=4, nz=4)
+    d = lbm.Domain(p)
+    with pytest.raises(lbm.LbmError) as ei:
+        d.set_kernel_config(64, 2)
+    assert ei.value.status == lbm.LBM_E_INVAL
+    d.init_tgv(1.0, 1.25, 1.0)
+    assert d.autotune(pairs_per_trial=1)["variant"] in (0, 1)  # staged forms not offered
+    d.close()
+    q = inputs.tgv_params(16)
+    q.update(nx=128, ny=4, nz=4)
+    e = lbm.Domain(q, store="f16")
+    e.init_tgv(1.0, 1.25, 1.0)
+    t = e.autotune(pairs_per_trial=1)
+    assert t["candidates"] == 7
+    e.close()
+
+
 def test_graphs_and_direct_launches_agree_bitwise(lbm):
     p = inputs.tgv_params(32)
     a = lbm.Domain(p, use_graphs=True)
