@@ -220,8 +220,11 @@ lbm_status lbm_synchronize(lbm_handle* h);
 
 /* Per-cell moments of the current (pre-collision) state: `which` = LBM_MOM_Q
  * (14 fields) or LBM_MOM_PRIM (6 fields), as [field][z][y][x] in `dtype`
- * (LBM_DT_F32 or LBM_DT_F64), into dst on the host or device. Decoded and summed
- * in FP64. Synchronises when dst is on the host. */
+ * (LBM_DT_F32 or LBM_DT_F64), into dst on the host or device. Populations decoded
+ * in FP32 as the step decodes them, summed in float-float pairs (about 48
+ * significant bits), shifted and closed in FP64. Synchronises when dst is on the
+ * host (through a device staging buffer the handle keeps, 256 MB, allocated on
+ * first use). */
 lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, int dtype);
 
 /* Sensor of the current state, [3][z][y][x]: theta = div u (physical units),
@@ -302,6 +305,14 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
  * reports LBM_E_CUDA from the next synchronising call and refuses further steps
  * until a re-init. */
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
+
+/* Failure-detection test hook (no counterpart in the paper). With a staged kernel form
+ * (variant 2-4), the next step does not issue the bulk copy of the first tile of one
+ * warp (block 0, warp 0), so that warp's bounded wait for it runs out after about a
+ * second; nothing faults or hangs. The step then ends early and the next
+ * synchronising call (lbm_synchronize, lbm_diag) returns LBM_E_CUDA, after which
+ * lbm_step refuses to run until a re-init. LBM_E_INVAL for a plain form. */
+lbm_status lbm_test_skip_copy(lbm_handle* h);
 
 /* ---- z-slab decomposition ------------------------------------------------------ */
 

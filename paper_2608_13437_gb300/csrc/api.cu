@@ -126,11 +126,11 @@ cudaError_t staged_prepare(const DomainConst& P, int store, int variant, int* gr
 }
 
 cudaError_t launch_step_staged(const DomainConst& P, int store, int parity, void* pop, unsigned* flag,
-                               int variant, int grid, cudaStream_t s) {
+                               int variant, int grid, int skip_first, cudaStream_t s) {
   switch (store) {
-    case LBM_STORE_F32: return launch_step_staged_f32(P, parity, pop, flag, variant, grid, s);
-    case LBM_STORE_F16: return launch_step_staged_f16(P, parity, pop, flag, variant, grid, s);
-    default: return launch_step_staged_bf16(P, parity, pop, flag, variant, grid, s);
+    case LBM_STORE_F32: return launch_step_staged_f32(P, parity, pop, flag, variant, grid, skip_first, s);
+    case LBM_STORE_F16: return launch_step_staged_f16(P, parity, pop, flag, variant, grid, skip_first, s);
+    default: return launch_step_staged_bf16(P, parity, pop, flag, variant, grid, skip_first, s);
   }
 }
 
@@ -171,6 +171,7 @@ struct lbm_handle {
   int variant = 0;             // step kernel: register budget (0, 1) or staged form (2-4)
   int staged_grid = 0;         // persistent grid of the staged forms
   bool stalled = false;        // a staged step gave up waiting for a bulk copy
+  bool skip_next_copy = false; // test hook: the next direct staged step skips one copy
   cudaGraphExec_t g_pair = nullptr, g_chunk = nullptr;
   bool graphs_valid = false;
   float* ufield = nullptr;     // diagnostics scratch: 4 floats per cell
@@ -210,7 +211,7 @@ int effective_block(const lbm_handle* h) {
 cudaError_t step_launch(lbm_handle* h, int parity, cudaStream_t s) {
   if (h->variant >= kFirstStagedVariant)
     return launch_step_staged(h->P, h->prm.store, parity, h->pop, h->flag, h->variant,
-                              h->staged_grid, s);
+                              h->staged_grid, 0, s);
   return launch_step(h->P, h->prm.store, parity, h->pop, h->ghost, h->flag, effective_block(h),
                      h->variant, s);
 }
@@ -252,7 +253,13 @@ lbm_status ensure_graphs(lbm_handle* h) {
 }
 
 lbm_status direct_step(lbm_handle* h) {
-  LBM_CUDA(step_launch(h, (int)(h->step & 1), h->stream));
+  if (h->skip_next_copy && h->variant >= kFirstStagedVariant) {
+    h->skip_next_copy = false;
+    LBM_CUDA(launch_step_staged(h->P, h->prm.store, (int)(h->step & 1), h->pop, h->flag, h->variant,
+                                h->staged_grid, 1, h->stream));
+  } else {
+    LBM_CUDA(step_launch(h, (int)(h->step & 1), h->stream));
+  }
   h->step += 1;
   return LBM_OK;
 }
@@ -536,6 +543,10 @@ lbm_status lbm_step(lbm_handle* h, int n) {
       if (s != LBM_OK) return s;
     }
     return LBM_OK;
+  }
+  if (h->skip_next_copy) {  // the test hook needs a direct launch
+    lbm_status s0 = direct_step(h);
+    if (s0 != LBM_OK || --n == 0) return s0;
   }
   lbm_status s = ensure_graphs(h);
   if (s != LBM_OK) return s;
@@ -901,6 +912,13 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
     out->ms_per_step = best;
     out->candidates = tried;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_test_skip_copy(lbm_handle* h) {
+  if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  if (h->variant < kFirstStagedVariant) return fail(LBM_E_INVAL, "the kernel form is not staged");
+  h->skip_next_copy = true;
   return LBM_OK;
 }
 

@@ -3,8 +3,9 @@
 // step. The grid holds as many blocks as are resident on the GPU. Each block
 // stages every domain's constants in shared memory once; then each warp claims
 // items from a counter, an item being `tiles_per_item` consecutive 32-cell layout
-// tiles, until none are left. A tile's domain is found by binary search
-// in the per-domain tile prefix sums; no block-wide synchronisation happens after
+// tiles, until none are left. A tile's domain and the (x, y, z) of its first cell
+// come from a per-tile table (one 16-byte broadcast load instead of a search and
+// two divisions); no block-wide synchronisation happens after
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
 // update is the single-domain one. Items per warp, block size and register budget
 // come from the autotuner; the step pair is replayed from a CUDA graph.
@@ -24,7 +25,7 @@ namespace {
 template <int PARITY, int MINB, typename S>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
-                                                          const int* __restrict__ tile_prefix,
+                                                          const int4* __restrict__ tiles,
                                                           int ndom, int total_tiles,
                                                           int tiles_per_item,
                                                           unsigned* __restrict__ next_item,
@@ -32,14 +33,12 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
   extern __shared__ __align__(16) unsigned char smem[];
   DomainConst* sP = reinterpret_cast<DomainConst*>(smem);
   S** sPop = reinterpret_cast<S**>(sP + ndom);
-  int* sPrefix = reinterpret_cast<int*>(sPop + ndom);
   {
     const int words = ndom * (int)(sizeof(DomainConst) / 4);
     const int* src = reinterpret_cast<const int*>(consts);
     int* dst = reinterpret_cast<int*>(sP);
     for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
     for (int j = threadIdx.x; j < ndom; j += blockDim.x) sPop[j] = static_cast<S*>(pops[j]);
-    for (int j = threadIdx.x; j <= ndom; j += blockDim.x) sPrefix[j] = tile_prefix[j];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -54,23 +53,13 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
     if (lane == 0) claim = atomicAdd(next_item, 1u);
     const int t_end = min(total_tiles, (item + 1) * tiles_per_item);
     for (int t = item * tiles_per_item; t < t_end; ++t) {
-      int lo = 0, hi = ndom;  // sPrefix[lo] <= t < sPrefix[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (sPrefix[mid] <= t) lo = mid;
-        else hi = mid;
-      }
+      const int4 ti = __ldg(&tiles[t]);  // domain, x0, y0, z0 of the tile's first cell
+      const int lo = ti.x;
       const DomainConst& P = sP[lo];
-      const int first = (t - sPrefix[lo]) * kTile;
-      const int cell = first + lane;
-      if (cell >= P.ncell) continue;
-      // (x, y, z) of the tile's first cell (one division per tile), then this lane's
-      // by carrying x past the row end (several rows when nx < 32).
-      const unsigned yz0 = (unsigned)first / (unsigned)P.nx;
-      const unsigned z0 = yz0 / (unsigned)P.ny;
-      int x = first - (int)yz0 * P.nx + lane;
-      int y = (int)(yz0 - z0 * (unsigned)P.ny);
-      int z = (int)z0;
+      const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
+      if (first + lane >= P.ncell) continue;
+      // this lane's (x, y, z): carry x past the row end (several rows when nx < 32)
+      int x = ti.y + lane, y = ti.z, z = ti.w;
       while (x >= P.nx) {
         x -= P.nx;
         if (++y == P.ny) {
@@ -105,7 +94,7 @@ struct lbm_batch {
   DomainConst* d_consts = nullptr;
   void** d_pops = nullptr;
   unsigned* d_maxbits = nullptr;  // per-field maxima for the FP16 scales at init
-  int* d_prefix = nullptr;     // per-domain prefix sums of 32-cell tiles (n + 1)
+  int4* d_tiles = nullptr;     // per tile: domain and (x, y, z) of its first cell
   unsigned* d_counter = nullptr;  // work-item counter of the persistent kernel
   int total_tiles = 0;
   int tiles_per_item = 4;      // layout tiles a warp takes at a time
@@ -182,11 +171,11 @@ template <typename S>
 void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
   const dim3 g(b->grid), bl(b->block);
   if (b->variant) {
-    if (parity) k_batch_step<1, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    if (parity) k_batch_step<1, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
   } else {
-    if (parity) k_batch_step<1, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_prefix, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    if (parity) k_batch_step<1, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    else k_batch_step<0, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
   }
 }
 
@@ -280,19 +269,28 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   std::vector<int> prefix(n + 1, 0);
   for (int d = 0; d < n; ++d) prefix[d + 1] = prefix[d] + (int)b->P[d].ntile;
   b->total_tiles = prefix[n];
-  b->smem = sizeof(DomainConst) * n + sizeof(void*) * n + sizeof(int) * (n + 1);
+  b->smem = sizeof(DomainConst) * n + sizeof(void*) * n;
+  std::vector<int4> tiles((size_t)b->total_tiles);
+  for (int d = 0; d < n; ++d) {
+    const DomainConst& P = b->P[d];
+    for (long long j = 0; j < P.ntile; ++j) {
+      const long long first = j * kTile;
+      tiles[(size_t)prefix[d] + j] = make_int4(d, (int)(first % P.nx), (int)((first / P.nx) % P.ny),
+                                               (int)(first / ((long long)P.nx * P.ny)));
+    }
+  }
   if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pops, sizeof(void*) * n) != cudaSuccess ||
       cudaMalloc(&b->d_maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&b->d_prefix, sizeof(int) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size()) != cudaSuccess ||
       cudaMalloc(&b->d_counter, 64) != cudaSuccess ||
       cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
   }
   if (cudaMemcpy(b->d_pops, ptrs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "batch table upload failed"));
   lbm_status s = upload_consts(b);
@@ -312,7 +310,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->pool) cudaFree(b->pool);
   if (b->d_consts) cudaFree(b->d_consts);
   if (b->d_pops) cudaFree(b->d_pops);
-  if (b->d_prefix) cudaFree(b->d_prefix);
+  if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->d_maxbits) cudaFree(b->d_maxbits);
   if (b->flag) cudaFree(b->flag);

@@ -1,6 +1,7 @@
 // Outputs of the current state through the AA read map of its parity: per-cell
-// moments (FP64 sums), the sensor exactly as the next step computes it, and
-// canonical population arrays in and out.
+// moments (float-float sums, FP64 results), the sensor exactly as the next step
+// computes it, canonical population arrays in and out, and raw slot planes.
+#include "diag_device.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -19,8 +20,13 @@ __device__ __forceinline__ double read_dev64(const DomainConst& P, const S* pop,
   return Codec<S>::dec64(pop[read_pos(P, c, parity, k, i)], (double)P.scale[k]);
 }
 
-template <typename S>
-__global__ void k_moments(const DomainConst P, int parity, const S* __restrict__ pop,
+// Zeroth moments of cells [c0, c0 + cnt) through the AA read map of the step's parity:
+// the populations are decoded in FP32 exactly as the step decodes them (the step's own
+// vector loads), summed per field in float-float pairs (two-sum, about 48 bits; no
+// FP64 work per population, FP64 being slow here), and carried to FP64 for the
+// reference shift and, for the primitive set, an FP64 closure.
+template <typename S, int PARITY, bool HELD>
+__global__ void k_moments(const DomainConst P, const S* __restrict__ pop,
                           const float* __restrict__ ghost, int which, void* out, int out_f64,
                           long long c0, long long cnt) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < cnt;
@@ -29,11 +35,19 @@ __global__ void k_moments(const DomainConst P, int parity, const S* __restrict__
     int x, y, z;
     decompose(P, cell, x, y, z);
     const CellIndex c = make_index(P, x, y, z);
+    float d[kF][kQ];
+    load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
+    const int nq = which == 1 ? 5 : kF;  // the primitives need rho, rho u, E only
     double Q[kF];
+#pragma unroll
     for (int k = 0; k < kF; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < kQ; ++i) s += read_dev64(P, pop, ghost, c, parity, k, i);
-      Q[k] = s;
+      Q[k] = 0.0;
+      if (k < nq) {
+        FF a = {d[k][0], 0.0f};
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) ff_add(a, d[k][i]);
+        Q[k] = ff_value(a);
+      }
     }
     Q[0] += (double)P.rho_ref;
     Q[4] += (double)P.E_ref;
@@ -51,6 +65,19 @@ __global__ void k_moments(const DomainConst P, int parity, const S* __restrict__
       if (out_f64) static_cast<double*>(out)[(long long)j * cnt + r] = v[j];
       else static_cast<float*>(out)[(long long)j * cnt + r] = (float)v[j];
     }
+  }
+}
+
+template <typename S>
+void launch_moments_t(const DomainConst& P, int parity, const S* pop, const float* ghost, int which,
+                      void* out, int out_f64, long long c0, long long cnt, int grid, int block,
+                      cudaStream_t s) {
+  if (P.bc_x) {
+    if (parity) k_moments<S, 1, true><<<grid, block, 0, s>>>(P, pop, ghost, which, out, out_f64, c0, cnt);
+    else k_moments<S, 0, true><<<grid, block, 0, s>>>(P, pop, ghost, which, out, out_f64, c0, cnt);
+  } else {
+    if (parity) k_moments<S, 1, false><<<grid, block, 0, s>>>(P, pop, ghost, which, out, out_f64, c0, cnt);
+    else k_moments<S, 0, false><<<grid, block, 0, s>>>(P, pop, ghost, which, out, out_f64, c0, cnt);
   }
 }
 
@@ -159,9 +186,9 @@ cudaError_t launch_moments(const DomainConst& P, int store, int parity, const vo
                            long long cnt, cudaStream_t s) {
   const int block = 128, grid = grid_for(cnt, block);
   switch (store) {
-    case 0: k_moments<float><<<grid, block, 0, s>>>(P, parity, (const float*)pop, ghost, which, out, out_f64, c0, cnt); break;
-    case 1: k_moments<__half><<<grid, block, 0, s>>>(P, parity, (const __half*)pop, ghost, which, out, out_f64, c0, cnt); break;
-    default: k_moments<__nv_bfloat16><<<grid, block, 0, s>>>(P, parity, (const __nv_bfloat16*)pop, ghost, which, out, out_f64, c0, cnt); break;
+    case 0: launch_moments_t(P, parity, (const float*)pop, ghost, which, out, out_f64, c0, cnt, grid, block, s); break;
+    case 1: launch_moments_t(P, parity, (const __half*)pop, ghost, which, out, out_f64, c0, cnt, grid, block, s); break;
+    default: launch_moments_t(P, parity, (const __nv_bfloat16*)pop, ghost, which, out, out_f64, c0, cnt, grid, block, s); break;
   }
   return cudaGetLastError();
 }

@@ -31,18 +31,20 @@ cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const 
 // The same step with its reads staged through shared memory by bulk asynchronous copies
 // (step_staged_*.cu; variants 2, 3, 4). Only for periodic domains whose rows are whole
 // 32-cell tiles. prepare sets the kernels' shared-memory limit and returns the
-// persistent grid size (SMs x resident blocks, at most one warp per tile).
+// persistent grid size (SMs x resident blocks, at most one warp per tile). skip_first
+// is a failure-detection test hook (one warp's first copy is not issued, so its
+// bounded wait runs out and the step reports a stalled copy).
 constexpr int kFirstStagedVariant = 2, kLastStagedVariant = 4;
 inline bool staged_eligible(const DomainConst& P) { return P.bc_x == 0 && P.nx % 32 == 0; }
 cudaError_t staged_prepare_f32(const DomainConst& P, int variant, int* grid);
 cudaError_t staged_prepare_f16(const DomainConst& P, int variant, int* grid);
 cudaError_t staged_prepare_bf16(const DomainConst& P, int variant, int* grid);
 cudaError_t launch_step_staged_f32(const DomainConst& P, int parity, void* pop, unsigned* flag,
-                                   int variant, int grid, cudaStream_t s);
+                                   int variant, int grid, int skip_first, cudaStream_t s);
 cudaError_t launch_step_staged_f16(const DomainConst& P, int parity, void* pop, unsigned* flag,
-                                   int variant, int grid, cudaStream_t s);
+                                   int variant, int grid, int skip_first, cudaStream_t s);
 cudaError_t launch_step_staged_bf16(const DomainConst& P, int parity, void* pop, unsigned* flag,
-                                    int variant, int grid, cudaStream_t s);
+                                    int variant, int grid, int skip_first, cudaStream_t s);
 
 // The same step that also computes the diagnostics of the state it reads (step_diag_*.cu):
 // writes u and mu_local to ufield (4 floats per cell) and one record of 17 floats per

@@ -22,9 +22,9 @@
 
 namespace lbm {
 
-// Polls of a bounded stage wait; far beyond any copy's latency (copies finish in
-// microseconds), short enough that a stuck pipeline ends the kernel within seconds.
-constexpr uint32_t kStageWaitPolls = 1u << 20;
+// Limit of a stage wait: far beyond any copy's latency (copies finish in microseconds),
+// short enough that a stuck pipeline ends the kernel within about a second.
+constexpr uint64_t kStageWaitNs = 1000000000ull;
 // A stage holds 9 slot blocks: the 7 of the tile (even steps), or for odd steps the 7
 // blocks the tile reads plus the two x-edge blocks (slot 2 of the tile holding cell
 // x0 - 1 and slot 1 of the tile holding cell x0 + 32), so no lane leaves shared memory.
@@ -117,9 +117,12 @@ __device__ __forceinline__ void load_cell_staged(const DomainConst& P, const S* 
   for (int i = 3; i < kQ; ++i) load_dir<S>(P, sb, i, lane, d, i);
 }
 
+// skip_first: failure-detection test hook; block 0, warp 0 does not issue the copy of
+// its first tile, so its wait for that tile runs out.
 template <int PARITY, typename S, int W, int ST, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) k_step_staged(const DomainConst P, S* __restrict__ pop,
-                                                              unsigned* __restrict__ flag) {
+                                                              unsigned* __restrict__ flag,
+                                                              int skip_first) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   S* stages = reinterpret_cast<S*>(smem_raw) + (size_t)warp * ST * kStageElems;
@@ -140,9 +143,11 @@ __global__ void __launch_bounds__(W * 32, MINB) k_step_staged(const DomainConst 
   TileCursor cur, ahead;
   cur.start(P, wid * per + (wid < extra ? wid : extra));
   ahead = cur;
+  const bool skip = skip_first && blockIdx.x == 0 && warp == 0;
   long long issued = 0;
   for (; issued < ST - 1 && issued < count; ++issued) {
-    if (lane == 0) issue_tile<PARITY, S>(P, pop, ahead, stages + issued * kStageElems, &bar[issued]);
+    if (lane == 0 && !(skip && issued == 0))
+      issue_tile<PARITY, S>(P, pop, ahead, stages + issued * kStageElems, &bar[issued]);
     ahead.next(P);
   }
   long long k = 0;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_step_staged(const DomainConst 
       ahead.next(P);
       ++issued;
     }
-    if (!mbar_wait(&bar[stage], (uint32_t)((k / ST) & 1), kStageWaitPolls)) {
+    if (!mbar_wait(&bar[stage], (uint32_t)((k / ST) & 1), kStageWaitNs)) {
       stuck = true;
       break;
     }
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_step_staged(const DomainConst 
     // the block's shared memory is released.
     if (lane == 0) atomicOr(flag, 2u);
     for (long long kk = k; kk < issued; ++kk)
-      mbar_wait(&bar[kk % ST], (uint32_t)((kk / ST) & 1), kStageWaitPolls);
+      mbar_wait(&bar[kk % ST], (uint32_t)((kk / ST) & 1), kStageWaitNs);
   }
 }
 
@@ -231,11 +236,13 @@ cudaError_t staged_prepare_v(const DomainConst& P, int* grid) {
 
 template <typename S, int V>
 void staged_launch_v(const DomainConst& P, int parity, S* pop, unsigned* flag, int grid,
-                     cudaStream_t s) {
+                     int skip_first, cudaStream_t s) {
   using C = StagedCfg<V>;
   const size_t smem = staged_smem<S, V>();
-  if (parity) k_step_staged<1, S, C::W, C::ST, C::MINB><<<grid, C::W * 32, smem, s>>>(P, pop, flag);
-  else k_step_staged<0, S, C::W, C::ST, C::MINB><<<grid, C::W * 32, smem, s>>>(P, pop, flag);
+  if (parity)
+    k_step_staged<1, S, C::W, C::ST, C::MINB><<<grid, C::W * 32, smem, s>>>(P, pop, flag, skip_first);
+  else
+    k_step_staged<0, S, C::W, C::ST, C::MINB><<<grid, C::W * 32, smem, s>>>(P, pop, flag, skip_first);
 }
 
 template <typename S>
@@ -251,13 +258,13 @@ cudaError_t staged_prepare_t(const DomainConst& P, int variant, int* grid) {
 
 template <typename S>
 cudaError_t staged_launch_t(const DomainConst& P, int parity, void* pop, unsigned* flag, int variant,
-                            int grid, cudaStream_t s) {
+                            int grid, int skip_first, cudaStream_t s) {
   if (!staged_eligible(P) || grid < 1) return cudaErrorInvalidConfiguration;
   S* p = static_cast<S*>(pop);
   switch (variant) {
-    case 2: staged_launch_v<S, 2>(P, parity, p, flag, grid, s); break;
-    case 3: staged_launch_v<S, 3>(P, parity, p, flag, grid, s); break;
-    case 4: staged_launch_v<S, 4>(P, parity, p, flag, grid, s); break;
+    case 2: staged_launch_v<S, 2>(P, parity, p, flag, grid, skip_first, s); break;
+    case 3: staged_launch_v<S, 3>(P, parity, p, flag, grid, skip_first, s); break;
+    case 4: staged_launch_v<S, 4>(P, parity, p, flag, grid, skip_first, s); break;
     default: return cudaErrorInvalidConfiguration;
   }
   return cudaGetLastError();

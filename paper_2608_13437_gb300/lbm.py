@@ -90,6 +90,7 @@ _SIGNATURES = {
     "lbm_diag": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
     "lbm_diag_static": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
     "lbm_step_diag": (_IP, [_VP, _IP, ctypes.POINTER(LbmDiag)]),
+    "lbm_test_skip_copy": (_IP, [_VP]),
     "lbm_plane_get": (_IP, [_VP, _IP, _IP, _VP, _IP]),
     "lbm_plane_set": (_IP, [_VP, _IP, _IP, _VP, _IP]),
     "lbm_populations_get": (_IP, [_VP, _VP, _IP, _IP]),

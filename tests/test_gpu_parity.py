@@ -379,6 +379,38 @@ def test_staged_variants_need_whole_tile_rows(lbm):
     e.close()
 
 
+def test_staged_copy_wait_runs_out_and_is_reported(lbm):
+    """Failure detection without a fault: the test hook keeps one warp's first bulk copy
+    from being issued, so its bounded wait (about a second) runs out. The step ends, the
+    next synchronising call reports LBM_E_CUDA, further steps are refused, and after a
+    re-init the same handle steps exactly like a fresh one (the context stayed usable)."""
+    import time
+    p = inputs.tgv_params(32)
+    d = lbm.Domain(p)
+    assert lbm.lib().lbm_test_skip_copy(d.handle) == lbm.LBM_E_INVAL  # plain form
+    d.set_kernel_config(64, 2)
+    d.init_tgv(1.0, 1.25, 1.0)
+    assert lbm.lib().lbm_test_skip_copy(d.handle) == lbm.LBM_OK
+    t0 = time.time()
+    d.step(3)
+    with pytest.raises(lbm.LbmError) as ei:
+        d.synchronize()
+    assert ei.value.status == lbm.LBM_E_CUDA and "bulk copy" in str(ei.value)
+    assert time.time() - t0 < 30
+    with pytest.raises(lbm.LbmError) as ei:
+        d.step(1)
+    assert ei.value.status == lbm.LBM_E_CUDA
+    d.init_tgv(1.0, 1.25, 1.0)
+    d.step(7)
+    d.synchronize()
+    ref = lbm.Domain(p)
+    ref.init_tgv(1.0, 1.25, 1.0)
+    ref.step(7)
+    assert np.array_equal(d.populations("native").view(np.uint32), ref.populations("native").view(np.uint32))
+    d.close()
+    ref.close()
+
+
 def test_graphs_and_direct_launches_agree_bitwise(lbm):
     p = inputs.tgv_params(32)
     a = lbm.Domain(p, use_graphs=True)
