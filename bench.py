@@ -468,7 +468,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage legs")
     ap.add_argument("--only-batch", type=int, default=0, metavar="K",
-                    help="run only the batched-mode leg on the first K seeded domains")
+                    help="run only the batched-mode leg on the first K seeded domains "
+                         "(storage from --store)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -482,8 +483,8 @@ def main():
 
         from paper_2608_13437_gb300 import inputs, lbm
         torch.cuda.set_device(0)
-        print(json.dumps(batch_leg(torch, lbm, inputs, args.steps, args.warmup, args.only_batch)),
-              flush=True)
+        print(json.dumps(batch_leg(torch, lbm, inputs, args.steps, args.warmup, args.only_batch,
+                                   store=args.store)), flush=True)
         return
     run_gpu(args)
 

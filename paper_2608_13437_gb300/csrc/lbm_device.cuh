@@ -487,16 +487,20 @@ __device__ __forceinline__ float collide_cell(const DomainConst& P, float (&d)[k
       field_flux<float>(k, s, fx, fy, fz);
       const float e0 = mul(0.25f, D[k]), e1 = mul(0.125f, D[k]);
       const float ax = mul(P.half_inv_c, fx), ay = mul(P.half_inv_c, fy), az = mul(P.half_inv_c, fz);
-      float dS = 0.0f;
-      if (k >= 5) dS = mul(k < 11 ? P.src_R : P.src_q, D[k]);
-      const float s0 = mul(0.25f, dS), s1 = mul(0.125f, dS);
-      d[k][0] = add(fma_(om, sub(e0, d[k][0]), d[k][0]), s0);
-      d[k][1] = add(fma_(om, sub(add(e1, ax), d[k][1]), d[k][1]), s1);
-      d[k][2] = add(fma_(om, sub(sub(e1, ax), d[k][2]), d[k][2]), s1);
-      d[k][3] = add(fma_(om, sub(add(e1, ay), d[k][3]), d[k][3]), s1);
-      d[k][4] = add(fma_(om, sub(sub(e1, ay), d[k][4]), d[k][4]), s1);
-      d[k][5] = add(fma_(om, sub(add(e1, az), d[k][5]), d[k][5]), s1);
-      d[k][6] = add(fma_(om, sub(sub(e1, az), d[k][6]), d[k][6]), s1);
+      d[k][0] = fma_(om, sub(e0, d[k][0]), d[k][0]);
+      d[k][1] = fma_(om, sub(add(e1, ax), d[k][1]), d[k][1]);
+      d[k][2] = fma_(om, sub(sub(e1, ax), d[k][2]), d[k][2]);
+      d[k][3] = fma_(om, sub(add(e1, ay), d[k][3]), d[k][3]);
+      d[k][4] = fma_(om, sub(sub(e1, ay), d[k][4]), d[k][4]);
+      d[k][5] = fma_(om, sub(add(e1, az), d[k][5]), d[k][5]);
+      d[k][6] = fma_(om, sub(sub(e1, az), d[k][6]), d[k][6]);
+      if (k >= 5) {  // the relaxation source of tau and q (zero for rho, rho u, E)
+        const float dS = mul(k < 11 ? P.src_R : P.src_q, D[k]);
+        const float s0 = mul(0.25f, dS), s1 = mul(0.125f, dS);
+        d[k][0] = add(d[k][0], s0);
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) d[k][i] = add(d[k][i], s1);
+      }
     }
     float probe = 0.0f;
 #pragma unroll

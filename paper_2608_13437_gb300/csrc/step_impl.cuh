@@ -6,33 +6,146 @@
 
 namespace lbm {
 
+// Rows of whole tiles (nx a multiple of 32, x periodic): a warp's 32 cells are one
+// tile, and the tiles holding its neighbours are the same for all lanes (only the two
+// edge lanes of an x neighbour fall into the next tile). Their indices are computed
+// once per warp, so every population access is a warp-uniform tile base plus the
+// lane's offset.
+struct WarpTiles {
+  long long t, xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ WarpTiles warp_tiles(const DomainConst& P, int x0, int y, int z) {
+  const long long tpr = P.nx / kTile, tpp = tpr * P.ny;  // tiles per row, per plane
+  WarpTiles T;
+  T.t = x0 / kTile + tpr * ((long long)y + (long long)P.ny * z);
+  T.xm = x0 > 0 ? T.t - 1 : T.t + tpr - 1;
+  T.xp = x0 + kTile < P.nx ? T.t + 1 : T.t - (tpr - 1);
+  T.ym = y > 0 ? T.t - tpr : T.t + (tpp - tpr);
+  T.yp = y + 1 < P.ny ? T.t + tpr : T.t - (tpp - tpr);
+  T.zm = z > 0 ? T.t - tpp : T.t + (P.ntile - tpp);
+  T.zp = z + 1 < P.nz ? T.t + tpp : T.t - (P.ntile - tpp);
+  return T;
+}
+
+// Tile and lane of the cell one lattice link from this lane's cell along direction i
+// (i = 1..6: +x, -x, +y, -y, +z, -z), forward (toward = +1) or backward (-1).
+__device__ __forceinline__ void link_tile(const WarpTiles& T, int i, int toward, int lane,
+                                          long long& tile, int& ln) {
+  const int axis = (i - 1) >> 1;
+  const int s = ((i & 1) ? 1 : -1) * toward;  // +1: toward +axis
+  ln = lane;
+  if (axis == 0) {
+    if (s > 0) {
+      tile = lane < kTile - 1 ? T.t : T.xp;
+      ln = lane < kTile - 1 ? lane + 1 : 0;
+    } else {
+      tile = lane > 0 ? T.t : T.xm;
+      ln = lane > 0 ? lane - 1 : kTile - 1;
+    }
+  } else if (axis == 1) {
+    tile = s > 0 ? T.yp : T.ym;
+  } else {
+    tile = s > 0 ? T.zp : T.zm;
+  }
+}
+
+// load_cell for whole-tile rows: even steps read slot i of the own cell, odd steps
+// slot opp(i) of cell x - e_i.
+template <int PARITY, typename S>
+__device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __restrict__ pop,
+                                               const WarpTiles& T, int lane, float (&d)[kF][kQ]) {
+  using V4 = typename Codec<S>::V4;
+  using V2 = typename Codec<S>::V2;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    long long tile = T.t;
+    int ln = lane;
+    if (PARITY && i > 0) link_tile(T, i, -1, lane, tile, ln);
+    const int slot = PARITY ? opp(i) : i;
+    const S* base = pop + tile * kTileElems;
+    float v[kF];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      const V4 w = *reinterpret_cast<const V4*>(base + group_offset(slot, g, ln));
+      Codec<S>::dec4(w, P.scale + 4 * g, v + 4 * g);
+    }
+    const V2 w2 = *reinterpret_cast<const V2*>(base + group_offset(slot, 3, ln));
+    Codec<S>::dec2(w2, P.scale + 12, v + 12);
+#pragma unroll
+    for (int k = 0; k < kF; ++k) d[k][i] = v[k];
+  }
+}
+
+// store_cell for whole-tile rows: even steps write slot opp(i) of the own cell, odd
+// steps slot i of cell x + e_i.
+template <int PARITY, typename S>
+__device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restrict__ pop,
+                                                const WarpTiles& T, int lane,
+                                                const float (&d)[kF][kQ]) {
+  using V4 = typename Codec<S>::V4;
+  using V2 = typename Codec<S>::V2;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    long long tile = T.t;
+    int ln = lane;
+    if (PARITY && i > 0) link_tile(T, i, +1, lane, tile, ln);
+    const int slot = PARITY ? i : opp(i);
+    S* base = pop + tile * kTileElems;
+    float v[kF];
+#pragma unroll
+    for (int k = 0; k < kF; ++k) v[k] = d[k][i];
+#pragma unroll
+    for (int g = 0; g < 3; ++g)
+      *reinterpret_cast<V4*>(base + group_offset(slot, g, ln)) = Codec<S>::enc4(v + 4 * g, P.inv_scale + 4 * g);
+    *reinterpret_cast<V2*>(base + group_offset(slot, 3, ln)) = Codec<S>::enc2(v + 12, P.inv_scale + 12);
+  }
+}
+
 // MINB = resident 128-thread blocks per SM the register budget is sized for:
 // 3 -> at most 170 registers (no spills), 4 -> at most 128 (a few spilled words).
-template <int PARITY, typename S, bool HELD, int MINB>
+// ROWS: whole-tile rows (periodic x, nx a multiple of 32), addressed per warp.
+template <int PARITY, typename S, bool HELD, int MINB, bool ROWS>
 __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __restrict__ pop,
                                                     const float* __restrict__ ghost,
                                                     unsigned* __restrict__ flag) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= P.nx) return;
-  const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
   float d[kF][kQ];
-  load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
-  if (P.collide) {
-    const float probe = collide_cell<false>(P, d, nullptr);
-    if (!isfinite(probe)) atomicOr(flag, 1u);
+  if constexpr (ROWS) {
+    const int x0 = blockIdx.x * blockDim.x + (threadIdx.x & ~(kTile - 1));
+    if (x0 >= P.nx) return;  // whole warps (nx is a multiple of 32)
+    const int lane = threadIdx.x & (kTile - 1);
+    const WarpTiles T = warp_tiles(P, x0, blockIdx.y, blockIdx.z);
+    load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+    if (P.collide) {
+      const float probe = collide_cell<false>(P, d, nullptr);
+      if (!isfinite(probe)) atomicOr(flag, 1u);
+    }
+    store_cell_rows<PARITY, S>(P, pop, T, lane, d);
+  } else {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.nx) return;
+    const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
+    load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
+    if (P.collide) {
+      const float probe = collide_cell<false>(P, d, nullptr);
+      if (!isfinite(probe)) atomicOr(flag, 1u);
+    }
+    store_cell<PARITY, S>(P, pop, c, d);
   }
-  store_cell<PARITY, S>(P, pop, c, d);
 }
 
 template <typename S, int MINB>
 void launch_variant(const DomainConst& P, int parity, S* p, const float* ghost, unsigned* flag,
                     dim3 grid, dim3 block, cudaStream_t s) {
   if (P.bc_x) {
-    if (parity) k_step<1, S, true, MINB><<<grid, block, 0, s>>>(P, p, ghost, flag);
-    else k_step<0, S, true, MINB><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    if (parity) k_step<1, S, true, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, true, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
+  } else if (P.nx % kTile == 0) {
+    if (parity) k_step<1, S, false, MINB, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, false, MINB, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
   } else {
-    if (parity) k_step<1, S, false, MINB><<<grid, block, 0, s>>>(P, p, ghost, flag);
-    else k_step<0, S, false, MINB><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    if (parity) k_step<1, S, false, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, false, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
   }
 }
 
