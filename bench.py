@@ -184,9 +184,17 @@ def cpu_baseline(n_global, budget_s=15.0):
     side = 128
     steps = max(1, min(50, int(budget_s * rate * 1e6 / side ** 3)))
     mlups, secs, thr = time_oracle(n_global, side, steps, 0)
+    # the same code on one core, on a 64^3 window for about 3 s
+    from oracle.oracle import set_threads
+    r1, _, _ = time_oracle(n_global, 32, 1, 0, threads=1)
+    s1 = max(1, min(20, int(3.0 * r1 * 1e6 / 64 ** 3)))
+    one, secs1, _ = time_oracle(n_global, 64, s1, 0, threads=1)
+    set_threads(thr)
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
             "sample": f"FP64 oracle, {side}^3 window of the {n_global}^3 TGV, {steps} steps "
-                      f"({secs:.1f} s), OpenMP over z-planes"}
+                      f"({secs:.1f} s), OpenMP over z-planes",
+            "single_core": {"value": round(one, 3), "unit": "MLUPS",
+                            "sample": f"64^3 window, {s1} steps ({secs1:.1f} s), 1 thread"}}
 
 
 def run_reference(args):

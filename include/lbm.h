@@ -219,12 +219,13 @@ lbm_status lbm_synchronize(lbm_handle* h);
 /* ---- outputs ------------------------------------------------------------------- */
 
 /* Per-cell moments of the current (pre-collision) state: `which` = LBM_MOM_Q
- * (14 fields) or LBM_MOM_PRIM (6 fields), as [field][z][y][x] in `dtype`
- * (LBM_DT_F32 or LBM_DT_F64), into dst on the host or device. Populations decoded
- * in FP32 as the step decodes them, summed in float-float pairs (about 48
- * significant bits), shifted and closed in FP64. Synchronises when dst is on the
- * host (through a device staging buffer the handle keeps, 256 MB, allocated on
- * first use). */
+ * (14 fields) or LBM_MOM_PRIM (6 fields: rho, u_x, u_y, u_z, T, p), as
+ * [field][z][y][x] in `dtype` (LBM_DT_F32 or LBM_DT_F64), into dst on the host or
+ * device. Populations are decoded in FP32 as the step decodes them; Q is a
+ * float-float sum (about 48 significant bits) of the seven populations and the
+ * reference; the primitives are exactly the step's own (its FP32 sums and closure).
+ * Synchronises when dst is on the host (through a device staging buffer the handle
+ * keeps, 256 MB, allocated on first use). */
 lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, int dtype);
 
 /* Sensor of the current state, [3][z][y][x]: theta = div u (physical units),

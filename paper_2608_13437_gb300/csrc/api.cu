@@ -386,7 +386,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
   const size_t ghost_bytes = sizeof(float) * 2 * kF * (size_t)p->ny * p->nz;
   if (cudaMalloc(&h->ghost, ghost_bytes) != cudaSuccess || cudaMalloc(&h->flag, 64) != cudaSuccess ||
       cudaMalloc(&h->maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&h->sums, 4 * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&h->sums, kFieldSumDoubles * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of small device buffers failed"));
   }

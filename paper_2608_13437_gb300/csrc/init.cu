@@ -110,7 +110,13 @@ __global__ void k_init(const DomainConst P, const InitSpec sp, int mode, S* __re
   }
 }
 
-__global__ void k_field_means(const DomainConst P, const InitSpec sp, double* sums) {
+constexpr int kMeanBlocks = (kFieldSumDoubles - 2) / 2, kMeanThreads = 256;
+
+// Sums of rho and E of the caller's fields, in a fixed order (per thread, then a
+// shared-memory tree per block, then the blocks in order), so Q_ref is reproducible.
+__global__ void __launch_bounds__(kMeanThreads) k_field_sums(const DomainConst P, const InitSpec sp,
+                                                             double* __restrict__ partials) {
+  __shared__ double sh[2][kMeanThreads];
   double s_rho = 0.0, s_E = 0.0;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < P.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
@@ -119,14 +125,25 @@ __global__ void k_field_means(const DomainConst P, const InitSpec sp, double* su
     s_rho += Q[0];
     s_E += Q[4];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s_rho += __shfl_down_sync(0xffffffffu, s_rho, o);
-    s_E += __shfl_down_sync(0xffffffffu, s_E, o);
+  sh[0][threadIdx.x] = s_rho;
+  sh[1][threadIdx.x] = s_E;
+  __syncthreads();
+  for (int half = kMeanThreads / 2; half > 0; half >>= 1) {
+    if (threadIdx.x < half) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + half];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + half];
+    }
+    __syncthreads();
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&sums[0], s_rho);
-    atomicAdd(&sums[1], s_E);
-  }
+  if (threadIdx.x < 2) partials[2 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_field_sums_final(const double* __restrict__ partials, int nblocks,
+                                   double* __restrict__ sums) {
+  if (threadIdx.x >= 2) return;
+  double r = 0.0;
+  for (int b = 0; b < nblocks; ++b) r += partials[2 * b + threadIdx.x];
+  sums[threadIdx.x] = r;
 }
 
 int grid_for(long long n, int block) {
@@ -151,10 +168,10 @@ cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, i
 
 cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
                                cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
-  if (e != cudaSuccess) return e;
-  const int block = 256;
-  k_field_means<<<grid_for(P.ncell, block), block, 0, s>>>(P, spec, sums);
+  // sums holds 2 results followed by 2 * kMeanBlocks partials
+  double* partials = sums + 2;
+  k_field_sums<<<kMeanBlocks, kMeanThreads, 0, s>>>(P, spec, partials);
+  k_field_sums_final<<<1, 32, 0, s>>>(partials, kMeanBlocks, sums);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Outputs of the current state through the AA read map of its parity: per-cell
-// moments (float-float sums, FP64 results), the sensor exactly as the next step
-// computes it, canonical population arrays in and out, and raw slot planes.
+// moments (float-float sums) and primitives as the step computes them, the sensor
+// exactly as the next step computes it, canonical population arrays in and out, and
+// raw slot planes.
 #include "diag_device.cuh"
 #include "lbm_internal.h"
 
@@ -20,11 +21,11 @@ __device__ __forceinline__ double read_dev64(const DomainConst& P, const S* pop,
   return Codec<S>::dec64(pop[read_pos(P, c, parity, k, i)], (double)P.scale[k]);
 }
 
-// Zeroth moments of cells [c0, c0 + cnt) through the AA read map of the step's parity:
-// the populations are decoded in FP32 exactly as the step decodes them (the step's own
-// vector loads), summed per field in float-float pairs (two-sum, about 48 bits; no
-// FP64 work per population, FP64 being slow here), and carried to FP64 for the
-// reference shift and, for the primitive set, an FP64 closure.
+// Moments of cells [c0, c0 + cnt) through the AA read map of the step's parity, from
+// the step's own loads and FP32 decode. LBM_MOM_Q: per field a float-float sum of the
+// seven populations and the reference (two-sum, about 48 significant bits), widened to
+// the output type. LBM_MOM_PRIM: the primitives exactly as the step computes them (its
+// FP32 sums and closure). No FP64 arithmetic: FP64 here is only an output format.
 template <typename S, int PARITY, bool HELD>
 __global__ void k_moments(const DomainConst P, const S* __restrict__ pop,
                           const float* __restrict__ ghost, int which, void* out, int out_f64,
@@ -37,33 +38,36 @@ __global__ void k_moments(const DomainConst P, const S* __restrict__ pop,
     const CellIndex c = make_index(P, x, y, z);
     float d[kF][kQ];
     load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
-    const int nq = which == 1 ? 5 : kF;  // the primitives need rho, rho u, E only
-    double Q[kF];
+    if (which == 1) {
+      float Q[kF];
 #pragma unroll
-    for (int k = 0; k < kF; ++k) {
-      Q[k] = 0.0;
-      if (k < nq) {
+      for (int k = 0; k < kF; ++k) {
+        float t = d[k][0];
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) t = add(t, d[k][i]);
+        Q[k] = t;
+      }
+      Q[0] = add(Q[0], P.rho_ref);
+      Q[4] = add(Q[4], P.E_ref);
+      Prim<float> s;
+      closure<float>(Q, P.gm1, P.mu, P.visc0, P.heat0, P.inv_T_ref, P.sutherland, s);
+      const float v[6] = {s.rho, s.u[0], s.u[1], s.u[2], s.T, s.p};
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (out_f64) static_cast<double*>(out)[(long long)j * cnt + r] = (double)v[j];
+        else static_cast<float*>(out)[(long long)j * cnt + r] = v[j];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kF; ++k) {
         FF a = {d[k][0], 0.0f};
 #pragma unroll
         for (int i = 1; i < kQ; ++i) ff_add(a, d[k][i]);
-        Q[k] = ff_value(a);
+        if (k == 0) ff_add(a, P.rho_ref);
+        if (k == 4) ff_add(a, P.E_ref);
+        if (out_f64) static_cast<double*>(out)[(long long)k * cnt + r] = ff_value(a);
+        else static_cast<float*>(out)[(long long)k * cnt + r] = add(a.hi, a.lo);
       }
-    }
-    Q[0] += (double)P.rho_ref;
-    Q[4] += (double)P.E_ref;
-    double v[kF];
-    int nv = kF;
-    if (which == 1) {
-      Prim<double> s;
-      closure<double>(Q, P.gm1_64, 0.0, 0.0, 0.0, 1.0, 0, s);
-      v[0] = s.rho; v[1] = s.u[0]; v[2] = s.u[1]; v[3] = s.u[2]; v[4] = s.T; v[5] = s.p;
-      nv = 6;
-    } else {
-      for (int k = 0; k < kF; ++k) v[k] = Q[k];
-    }
-    for (int j = 0; j < nv; ++j) {
-      if (out_f64) static_cast<double*>(out)[(long long)j * cnt + r] = v[j];
-      else static_cast<float*>(out)[(long long)j * cnt + r] = (float)v[j];
     }
   }
 }

@@ -79,7 +79,9 @@ struct InitSpec {
 // the encoded populations (canonical slots) and the held-x ghost layers.
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
                         float* ghost, unsigned* maxbits, cudaStream_t s);
-// Sums of rho and E over the caller fields (kind 2 or 3) into sums[2] (zeroed here).
+// Sums of rho and E over the caller fields (kind 2 or 3) into sums[0..2), in a fixed
+// order; sums must hold kFieldSumDoubles doubles (the rest is block scratch).
+constexpr int kFieldSumDoubles = 2 + 2 * 1216;
 cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
                                cudaStream_t s);
 
