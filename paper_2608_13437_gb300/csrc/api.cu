@@ -102,10 +102,6 @@ void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, Doma
   P->sensor_mode = p->sensor_mode;
   P->collide = p->collide;
   P->dx64 = p->dx;
-  P->dt64 = dt;
-  P->mu64 = p->mu;
-  P->inv_T_ref64 = 1.0 / p->T_ref;
-  P->gm1_64 = p->gamma - 1.0;
 }
 
 cudaError_t launch_step(const DomainConst& P, int store, int parity, void* pop, const float* ghost,

@@ -1,7 +1,8 @@
 // Diagnostics of the current state (Sec. 3.2, Eq. 7): conservation sums,
 // <rho|u|^2/2>, <mu_local |curl u|^2>, 4/3 <mu_local (div u)^2>, extrema and a
 // non-finite count. Per-cell work runs in FP32 exactly as in the step (the moments and
-// closure come from collide_cell itself); FP64 holds the sums. Pass A decodes every
+// closure come from collide_cell itself); sums are float-float pairs, widened to FP64
+// once per block. Pass A decodes every
 // cell and keeps u and mu_local in a scratch field (4 floats per cell); the step
 // kernel's diagnostic variant fills the same field and writes one record per warp
 // instead (step_diag.cuh), which pass R folds into per-block records. Pass B takes

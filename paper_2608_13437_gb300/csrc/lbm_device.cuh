@@ -45,7 +45,7 @@ struct DomainConst {
   float rho_ref, E_ref;
   float scale[kF], inv_scale[kF];
   int sutherland, sensor_mode, collide, pad_;
-  double dx64, dt64, mu64, inv_T_ref64, gm1_64;  // FP64 copies for the diagnostics
+  double dx64;        // dx in FP64 (the diagnostics' gradient pass takes 1/dx from it)
 };
 
 // ---------------------------------------------------------------- storage codecs

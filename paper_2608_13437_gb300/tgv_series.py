@@ -1,5 +1,6 @@
 """Time series of the supersonic Taylor-Green vortex (Sec. 3.2): kinetic energy and
-the solenoidal and dilatational dissipation rates (Eq. 7) from the FP64 diagnostics.
+the solenoidal and dilatational dissipation rates (Eq. 7), computed inside the step
+every `every` steps (lbm_step_diag; FP64 global sums).
 
     python -m paper_2608_13437_gb300.tgv_series --n 256 --steps 20000 --every 100 \
         [--store f32] [--M0 1.25] [--Re 1000] [--out series.json]
@@ -26,8 +27,7 @@ def run(n: int, steps: int, every: int, store: str = "f32", M0: float = 1.25, Re
     dom.init_tgv(U0, M0, rho0)
     samples = []
 
-    def sample():
-        d = dom.diag()
+    def sample(d):
         if d["status"] != lbm.LBM_OK:
             raise RuntimeError(f"non-finite state at step {d['step']:.0f}")
         samples.append({"step": int(d["step"]), "t_c": d["time"] * U0 / 1.0,
@@ -36,13 +36,13 @@ def run(n: int, steps: int, every: int, store: str = "f32", M0: float = 1.25, Re
                         "max_mach": d["max_mach"], "max_cfl": d["max_cfl"]})
 
     t0 = time.perf_counter()
-    sample()
     done = 0
     while done < steps:
         k = min(every, steps - done)
-        dom.step(k)
+        # the first of these k steps also computes the diagnostics of the state it reads
+        sample(dom.step_diag(k))
         done += k
-        sample()
+    sample(dom.diag())  # the final state
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     info = dom.info()
