@@ -74,3 +74,39 @@ def test_null_arguments_are_rejected(L):
     assert L.lbm_destroy(None) == lbm.LBM_OK
     assert L.lbm_status_string(4) == b"LBM_E_NONFINITE"
     assert L.lbm_batch_create(0, None, ctypes.byref(ctypes.c_void_p())) == lbm.LBM_E_INVAL
+
+
+def test_every_entry_point_rejects_a_null_handle(L):
+    """No entry point dereferences a NULL handle or output pointer: each returns
+    LBM_E_INVAL (lbm_destroy and lbm_batch_destroy accept NULL) before any CUDA call."""
+    from paper_2608_13437_gb300 import lbm
+    V = None
+    buf = ctypes.create_string_buffer(64)
+    d3 = (ctypes.c_double * 3)(1.0, 0.0, 1.0)
+    calls = {
+        "lbm_get_info": (V, V), "lbm_init_tgv": (V, 1.0, 1.25, 1.0),
+        "lbm_init_riemann": (V, 0, 1, d3, d3), "lbm_init_fields": (V, buf, 0, 0),
+        "lbm_init_state": (V, buf, 0, 0), "lbm_step": (V, 1), "lbm_synchronize": (V,),
+        "lbm_moments": (V, 0, buf, 0, 0), "lbm_sensor": (V, buf, 0, 0), "lbm_diag": (V, V),
+        "lbm_step_diag": (V, 1, V), "lbm_diag_static": (V, V),
+        "lbm_populations_get": (V, buf, 0, 0), "lbm_populations_set": (V, buf, 0, 0),
+        "lbm_save": (V, b"x"), "lbm_load": (V, b"x"), "lbm_autotune": (V, 1, V),
+        "lbm_set_kernel_config": (V, 64, 0), "lbm_test_skip_copy": (V,),
+        "lbm_plane_get": (V, 0, 0, buf, 0), "lbm_plane_set": (V, 0, 0, buf, 0),
+        "lbm_batch_init_tgv": (V, d3, d3, d3), "lbm_batch_step": (V, 1),
+        "lbm_batch_step_sequential": (V, 1), "lbm_batch_synchronize": (V,),
+        "lbm_batch_moments": (V, 0, 0, buf, 0, 0), "lbm_batch_info": (V, V, 0, V),
+        "lbm_batch_autotune": (V, 1, V, V, V),
+    }
+    for name, args in calls.items():
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_int
+        assert fn(*args) == lbm.LBM_E_INVAL, name
+    assert L.lbm_destroy(None) == lbm.LBM_OK
+    assert L.lbm_batch_destroy(None) == lbm.LBM_OK
+    declared = set(_declared())
+    untested = declared - set(calls) - {"lbm_create", "lbm_destroy", "lbm_batch_create",
+                                        "lbm_batch_destroy", "lbm_population_bytes",
+                                        "lbm_last_error", "lbm_status_string"}
+    assert not untested, untested
+
