@@ -7,7 +7,8 @@
 // come from a per-tile table (one 16-byte broadcast load instead of a search and
 // two divisions); no block-wide synchronisation happens after
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
-// update is the single-domain one. Items per warp, block size and register budget
+// update is the single-domain one; domains whose rows are whole tiles use its
+// warp-uniform tile addressing. Items per warp, block size and register budget
 // come from the autotuner; the step pair is replayed from a CUDA graph.
 #include <algorithm>
 #include <cmath>
@@ -16,6 +17,7 @@
 #include <vector>
 
 #include "api_common.h"
+#include "step_impl.cuh"
 
 using namespace lbm;
 
@@ -56,6 +58,17 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
       const int4 ti = __ldg(&tiles[t]);  // domain, x0, y0, z0 of the tile's first cell
       const int lo = ti.x;
       const DomainConst& P = sP[lo];
+      S* pop = sPop[lo];
+      float d[kF][kQ];
+      if ((P.nx & (kTile - 1)) == 0) {
+        // whole-tile rows: the tile and its neighbour tiles are warp-uniform
+        const WarpTiles T = warp_tiles(P, ti.y, ti.z, ti.w);
+        load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+        const float probe = collide_cell<false>(P, d, nullptr);
+        if (!isfinite(probe)) atomicOr(flag, 1u);
+        store_cell_rows<PARITY, S>(P, pop, T, lane, d);
+        continue;
+      }
       const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
       if (first + lane >= P.ncell) continue;
       // this lane's (x, y, z): carry x past the row end (several rows when nx < 32)
@@ -68,8 +81,6 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
         }
       }
       const CellIndex c = make_index(P, x, y, z);
-      S* pop = sPop[lo];
-      float d[kF][kQ];
       load_cell<PARITY, false, S>(P, pop, nullptr, c, d);
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
