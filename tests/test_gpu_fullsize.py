@@ -88,6 +88,34 @@ def test_512_staged_form_and_in_step_diagnostics(lbm):
     a.close()
 
 
+def test_dissipation_curves_per_storage_type(lbm, oracle_mod):
+    """Time series of E_k, eps_s and eps_d (Eq. 7), sampled inside the step every 50
+    steps over 400 steps of the 64^3 TGV, for each storage type against the FP64
+    oracle's; the error is the largest deviation over the curve divided by the curve's
+    largest value. Observed: FP32 1e-7..4e-7, FP16 7e-5..2.4e-4, BF16 1.7e-3..1.4e-2."""
+    n, every, steps = 64, 50, 400
+    p = inputs.tgv_params(n)
+    o = make_oracle(p)
+    o.init_tgv(1.0, 1.25, 1.0)
+    ref = []
+    for k in range(steps // every + 1):
+        ref.append(o.diag())
+        if k < steps // every:
+            o.step(every)
+    bounds = {"f32": 2e-6, "f16": 1e-3, "bf16": 5e-2}
+    for store, bound in bounds.items():
+        d = lbm.Domain(p, store=store)
+        d.init_tgv(1.0, 1.25, 1.0)
+        got = [d.step_diag(every) for _ in range(steps // every)] + [d.diag()]
+        d.close()
+        assert [g["step"] for g in got] == [r["step"] for r in ref]
+        for key in ("ek_mean", "eps_s_raw", "eps_d_raw"):
+            a = np.array([g[key] for g in got])
+            b = np.array([r[key] for r in ref])
+            err = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+            assert err < bound, (store, key, err)
+
+
 def test_sod_convergence_gpu(lbm):
     """Sec. 3.1, Tables 2 and 4: the captured shock thickness holds a fixed number of
     cells (w proportional to dx, first order), the shock sits within 1e-3 of the exact
