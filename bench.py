@@ -355,6 +355,13 @@ def run_gpu(args):
     ms_max = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_max / args.steps
     value = job_value(world, ncell, args.steps, ms_max)
+    # two shorter windows on the evolved state: best and median of three, as context
+    # for run-to-run spread (the value above is the K-step window alone)
+    rep_steps = max(2, min(args.steps, 500) // 2 * 2)
+    repeats = [round(value, 1)]
+    for _ in range(2):
+        ms_r, _ = time_steps(torch, dom, rep_steps, 2, dist)
+        repeats.append(round(job_value(world, ncell, rep_steps, reduce_max(ms_r, dist, "cuda")), 1))
     hbm, peak_kind = peaks()
     bpc = BYTES_PER_CELL[args.store]
     achieved = bpc * ncell / (ms_total / args.steps * 1e-3) / 1e9
@@ -394,8 +401,8 @@ def run_gpu(args):
     e2e = {"value": round(job_value(world, ncell, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(fields.numel() * 4 / args.steps),
            "d2h_bytes_per_step": int((out.numel() * 4 + len(series) * 15 * 8) / args.steps),
-           "api": "lbm_init_fields(host) + lbm_step_diag every 50 steps (FP64 diagnostics "
-                  "computed in the step) + lbm_moments(host)",
+           "api": "lbm_init_fields(host) + lbm_step_diag every 50 steps (diagnostics "
+                  "computed in the step, FP64 global sums) + lbm_moments(host)",
            "diagnostics": len(series), "phases_gpu_ms": phases,
            "ek_last": series[-1]["ek_mean"] if series else None}
     diag_cost = None
@@ -453,6 +460,8 @@ def run_gpu(args):
                        "l2": "populations (%.1f GB) exceed the 129 MB L2; no flush between steps"
                              % (BYTES_PER_CELL[args.store] / 2 * ncell / 1e9)},
             "roofline": roofline,
+            "repeats": {"MLUPS": repeats, "best": max(repeats),
+                        "median": sorted(repeats)[1], "steps": [args.steps, rep_steps, rep_steps]},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

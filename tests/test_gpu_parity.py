@@ -449,20 +449,36 @@ def test_kernel_configurations_agree_bitwise(lbm, store):
             assert np.array_equal(f, ref), (bx, var)
 
 
-def test_checkpoint_resume_is_bit_identical(lbm):
-    p = inputs.tgv_params(16)
-    a = lbm.Domain(p)
-    a.init_tgv(1.0, 1.25, 1.0)
+@pytest.mark.parametrize("case,store", [("tgv", "f32"), ("tgv", "f16"), ("sod", "bf16")])
+def test_checkpoint_resume_is_bit_identical(lbm, case, store):
+    """Save after an odd number of steps, keep going, load into a fresh handle and
+    take the same steps: identical bits. Covers the FP16 per-field scales, Q_ref and
+    the held-x ghost layers (Sod)."""
+    if case == "tgv":
+        p = inputs.tgv_params(16)
+    else:
+        p = inputs.sod_params(64)
+    a = lbm.Domain(p, store=store)
+    if case == "tgv":
+        a.init_tgv(1.0, 1.25, 1.0)
+    else:
+        a.init_riemann(0, 32, inputs.SOD_LEFT, inputs.SOD_RIGHT)
     a.step(13)
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "ck.bin")
         a.save(path)
         a.step(10)
-        b = lbm.Domain(p)
+        b = lbm.Domain(p, store=store)
         b.load(path)
         assert b.info()["step"] == 13
+        assert b.info()["scale"] == a.info()["scale"]
         b.step(10)
         assert np.array_equal(a.populations("native"), b.populations("native"))
+        other = lbm.Domain(p, store="f32" if store != "f32" else "f16")
+        with pytest.raises(lbm.LbmError) as ei:
+            other.load(path)
+        assert ei.value.status == lbm.LBM_E_INVAL
+        other.close()
         with open(path, "r+b") as fh:  # corrupt one byte: the CRC must catch it
             fh.seek(4000)
             byte = fh.read(1)
