@@ -76,9 +76,9 @@ def dist_ring_shift(t, shift: int, dist, group=None):
 
 
 class SlabRing:
-    """Slab handles of one domain held in one process (one device or several),
-    stepped with the AA exchanges through lbm_plane_get / lbm_plane_set on device
-    buffers. The handles must share Q_ref and storage scales (e.g. FP32 or BF16
+    """Slab handles of one domain held in one process (one device or several; planes
+    move between devices as tensor copies), stepped with the AA exchanges through
+    lbm_plane_get / lbm_plane_set on device buffers. The handles must share Q_ref and storage scales (e.g. FP32 or BF16
     storage initialised with lbm_init_tgv, then loaded with their part of one state)."""
 
     def __init__(self, domains: list):
@@ -98,7 +98,8 @@ class SlabRing:
             for d in self.domains:
                 torch.cuda.synchronize(d.device)
             for d, buf in zip(self.domains, ring_shift(planes, shift)):
-                d.plane_set(plane_index(which, d.nz), slot, buf)
+                # a plane from a slab on another device is copied to this one first
+                d.plane_set(plane_index(which, d.nz), slot, buf.to(d.device))
             for d in self.domains:
                 torch.cuda.synchronize(d.device)
 
