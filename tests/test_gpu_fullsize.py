@@ -3,8 +3,13 @@
     cone: after n steps a cell depends only on cells within n lattice steps, so the
     oracle recomputes a (B + 2n)^3 window of the same initial field and its central
     B^3 cells must match the GPU's (sampled outputs at full size);
+  * 512^3: the TMA-staged step form against the plain kernel (bit for bit, on the
+    device) and the in-step diagnostics against the separate pass;
+  * dissipation time series per storage type against the oracle (64^3, 400 steps);
   * Sod at 256..2048 cells: shock position, first-order thickness, L1 falling;
-  * reduced storage at 128^3 against the FP64 oracle and the FP32 GPU path.
+  * reduced storage at 128^3 against the FP64 oracle and the FP32 GPU path;
+  * Becker's viscous shock against the exact profile, the oracle and Table 3;
+  * spectral diagnostics against the oracle's.
 """
 import numpy as np
 import pytest
