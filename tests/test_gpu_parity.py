@@ -154,13 +154,16 @@ def test_sensor_matches_oracle_on_same_state(lbm, oracle_mod):
     dom.close()
 
 
-def test_sod_matches_oracle_and_exact(lbm, oracle_mod):
+@pytest.mark.parametrize("store,mean_bound", [("f32", 1e-4), ("f16", 3e-2), ("bf16", 5e-2)])
+def test_sod_matches_oracle_and_exact(lbm, oracle_mod, store, mean_bound):
     """Sod on 1024 x 4 x 4, x ends held, to t = 0.2: shock position within 1e-3 of
-    the oracle's and of the exact solution; density profile close to the oracle's."""
+    the oracle's and of the exact solution; density profile close to the oracle's.
+    Mean density deviation observed: FP32 1.1e-5; FP16 1.2e-2 and BF16 1.7e-2, the
+    storage rounding of ~1300 steps (the shock stays within 1e-3 in all three)."""
     from oracle import riemann
     n = 1024
     p = inputs.sod_params(n)
-    dom = lbm.Domain(p)
+    dom = lbm.Domain(p, store=store)
     dom.init_riemann(0, n // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
     steps = inputs.sod_steps(dom.dt)
     dom.step(steps)
@@ -188,7 +191,8 @@ def test_sod_matches_oracle_and_exact(lbm, oracle_mod):
                                       riemann.State(*inputs.SOD_RIGHT), t, 0.5)
     assert abs(shock(rho_g) - shock(rho_o)) < 1e-3
     assert abs(shock(rho_g) - xs_exact) < 1e-3
-    assert np.mean(np.abs(rho_g - rho_o)) < 1e-3
+    dev = float(np.mean(np.abs(rho_g - rho_o)))
+    assert dev < mean_bound, dev
     dom.close()
 
 
