@@ -97,6 +97,11 @@ typedef struct {
                             non-equilibrium moments; 1: div(rho u)/rho only */
   int collide;           /* 1: collide and stream; 0: stream only (tests) */
   int store;             /* lbm_store */
+  int stochastic_round;  /* 16-bit storage only: 1 rounds every stored population up or
+                            down at random with the probabilities that make the rounding
+                            unbiased (random bits from the cell's index and state, so the
+                            result is reproducible); 0 rounds to nearest (default). Not
+                            with the staged kernel forms or the batched mode */
   int use_graphs;        /* 1: lbm_step replays captured CUDA graphs of whole step pairs */
   void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
   void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
@@ -300,8 +305,8 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
 /* Fixes the step kernel's form (variant 0-4, see lbm_info_t) and, for variants 0 and
  * 1, its block size (32, 64, 96 or 128 threads; ignored by the staged variants)
  * instead of the defaults or the autotuner's choice. The staged variants need a
- * periodic x axis and nx a multiple of 32 (whole 32-cell tiles per row; LBM_E_INVAL
- * otherwise). All forms compute bit-identical populations. A staged step whose wait
+ * periodic x axis, nx a multiple of 32 (whole 32-cell tiles per row) and rounding to
+ * nearest (LBM_E_INVAL otherwise). All forms compute bit-identical populations. A staged step whose wait
  * for a copy runs out (bounded; it does not happen in normal operation) stops,
  * reports LBM_E_CUDA from the next synchronising call and refuses further steps
  * until a re-init. */

@@ -55,6 +55,8 @@ lbm_status validate(const lbm_params* p) {
   if (!(p->omega_min > 0.0 && p->omega_min <= 2.0))
     return fail(LBM_E_INVAL, "omega_min must lie in (0, 2]");
   if (p->store < 0 || p->store > 2) return fail(LBM_E_INVAL, "store must be 0, 1 or 2");
+  if (p->stochastic_round < 0 || p->stochastic_round > 1)
+    return fail(LBM_E_INVAL, "stochastic_round must be 0 or 1");
   if (p->bc_x < 0 || p->bc_x > 1) return fail(LBM_E_INVAL, "bc_x must be 0 or 1");
   if (p->source_mode < 0 || p->source_mode > 1) return fail(LBM_E_INVAL, "source_mode must be 0 or 1");
   if (p->sensor_mode < 0 || p->sensor_mode > 1) return fail(LBM_E_INVAL, "sensor_mode must be 0 or 1");
@@ -101,6 +103,7 @@ void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, Doma
   P->sutherland = p->sutherland;
   P->sensor_mode = p->sensor_mode;
   P->collide = p->collide;
+  P->sround = p->stochastic_round;
   P->dx64 = p->dx;
 }
 
@@ -923,7 +926,8 @@ lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
   if (variant < 0 || variant > kLastStagedVariant) return fail(LBM_E_INVAL, "variant must be 0 to 4");
   if (variant >= kFirstStagedVariant) {
     if (!staged_eligible(h->P))
-      return fail(LBM_E_INVAL, "staged variants need periodic x and nx a multiple of 32");
+      return fail(LBM_E_INVAL,
+                  "staged variants need periodic x, nx a multiple of 32 and rounding to nearest");
     int grid = 0;
     LBM_CUDA(staged_prepare(h->P, h->prm.store, variant, &grid));
     h->variant = variant;

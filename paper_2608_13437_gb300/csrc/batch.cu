@@ -250,6 +250,10 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
     }
+    if (params[d].stochastic_round != 0) {
+      delete b;
+      return fail(LBM_E_INVAL, "domain %d: the batched mode rounds to nearest (stochastic_round = 0)", d);
+    }
     b->prm.push_back(params[d]);
     double dt, tR, tq;
     derive(&params[d], &dt, &tR, &tq);

@@ -13,6 +13,8 @@
 // runs in single precision), so every sum below works on small numbers.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -44,7 +46,8 @@ struct DomainConst {
   float src_R, src_q; // dS_k = src * Q_k for tau and q fields
   float rho_ref, E_ref;
   float scale[kF], inv_scale[kF];
-  int sutherland, sensor_mode, collide, pad_;
+  int sutherland, sensor_mode, collide;
+  int sround;         // 16-bit storage rounds stochastically (1) or to nearest (0)
   double dx64;        // dx in FP64 (the diagnostics' gradient pass takes 1/dx from it)
 };
 
@@ -102,6 +105,36 @@ struct Codec16 {
   static __device__ __forceinline__ V2 enc2(const float i[2], const float* is) {
     if (!kScaled) return from_f2(i[0], i[1]);
     return from_f2(i[0] * is[0], i[1] * is[1]);
+  }
+  // Stochastic rounding: the float's bits below the 16-bit format's last place (13 for
+  // FP16, 16 for BF16) get a random addend before they are cut off, so a value is
+  // rounded away from zero with probability equal to its distance from the value
+  // below; the cut value is exact in the 16-bit format (normal range), so the
+  // conversion that follows changes nothing. r supplies the addend in its low bits.
+  static constexpr int kCut = kScaled ? 13 : 16;
+  static __device__ __forceinline__ float sr_cut(float x, unsigned r) {
+    constexpr unsigned mask = (1u << kCut) - 1u;
+    return __uint_as_float((__float_as_uint(x) + (r & mask)) & ~mask);
+  }
+  static __device__ __forceinline__ V4 enc4_sr(const float i[4], const float* is, unsigned r0,
+                                               unsigned r1) {
+    float a = i[0], b = i[1], c = i[2], e = i[3];
+    if (kScaled) {
+      a = a * is[0];
+      b = b * is[1];
+      c = c * is[2];
+      e = e * is[3];
+    }
+    return make_uint2(from_f2(sr_cut(a, r0), sr_cut(b, r0 >> 16)),
+                      from_f2(sr_cut(c, r1), sr_cut(e, r1 >> 16)));
+  }
+  static __device__ __forceinline__ V2 enc2_sr(const float i[2], const float* is, unsigned r) {
+    float a = i[0], b = i[1];
+    if (kScaled) {
+      a = a * is[0];
+      b = b * is[1];
+    }
+    return from_f2(sr_cut(a, r), sr_cut(b, r >> 16));
   }
 };
 
@@ -265,26 +298,73 @@ __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restr
   }
 }
 
-// Stores the 98 post-collision deviations: direction i goes to the slot and cell of
-// the AA map (own cell, slot opp(i) on even steps; cell x + e_i, slot i on odd steps).
-template <int PARITY, typename S>
-__device__ __forceinline__ void store_cell(const DomainConst& P, S* __restrict__ pop,
-                                           const CellIndex& c, const float (&d)[kF][kQ]) {
+// Random words for stochastic rounding, one stream per cell and step: seeded from the
+// cell's index and the bits of two of its post-collision populations (so the stream
+// changes as the state evolves, and every kernel form draws the same words for the
+// same cell), then advanced by Marsaglia's xorshift32.
+struct Dither {
+  unsigned s;
+  __device__ __forceinline__ Dither(long long cell, float a, float b) {
+    unsigned x = (unsigned)cell * 0x9E3779B1u;
+    x ^= __float_as_uint(a) * 0x85EBCA77u;
+    x ^= __float_as_uint(b) * 0xC2B2AE3Du;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 13;
+    s = x | 1u;  // xorshift32 needs a non-zero state
+  }
+  __device__ __forceinline__ unsigned next() {
+    s ^= s << 13;
+    s ^= s >> 17;
+    s ^= s << 5;
+    return s;
+  }
+};
+
+// One direction's 14 fields into the 4 + 4 + 4 + 2 groups of slot `slot`, lane `lane`
+// of the tile at `base`, rounded to nearest or (dz != nullptr) stochastically.
+template <typename S>
+__device__ __forceinline__ void store_dir(const DomainConst& P, S* base, int slot, int lane,
+                                          const float (&d)[kF][kQ], int i, Dither* dz) {
   using V4 = typename Codec<S>::V4;
   using V2 = typename Codec<S>::V2;
+  float v[kF];
+#pragma unroll
+  for (int k = 0; k < kF; ++k) v[k] = d[k][i];
+  if constexpr (!std::is_same<S, float>::value) {
+    if (dz) {
+#pragma unroll
+      for (int g = 0; g < 3; ++g) {
+        const unsigned r0 = dz->next(), r1 = dz->next();
+        *reinterpret_cast<V4*>(base + group_offset(slot, g, lane)) =
+            Codec<S>::enc4_sr(v + 4 * g, P.inv_scale + 4 * g, r0, r1);
+      }
+      *reinterpret_cast<V2*>(base + group_offset(slot, 3, lane)) =
+          Codec<S>::enc2_sr(v + 12, P.inv_scale + 12, dz->next());
+      return;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+    *reinterpret_cast<V4*>(base + group_offset(slot, g, lane)) = Codec<S>::enc4(v + 4 * g, P.inv_scale + 4 * g);
+  *reinterpret_cast<V2*>(base + group_offset(slot, 3, lane)) = Codec<S>::enc2(v + 12, P.inv_scale + 12);
+}
+
+// Stores the 98 post-collision deviations: direction i goes to the slot and cell of
+// the AA map (own cell, slot opp(i) on even steps; cell x + e_i, slot i on odd steps).
+// SR: stochastic rounding of 16-bit storage (a separate instantiation, so the
+// round-to-nearest kernels carry none of its code).
+template <int PARITY, typename S, bool SR = false>
+__device__ __forceinline__ void store_cell(const DomainConst& P, S* __restrict__ pop,
+                                           const CellIndex& c, const float (&d)[kF][kQ]) {
+  [[maybe_unused]] Dither dz(0, 0.0f, 0.0f);
+  if constexpr (SR) dz = Dither(c.own, d[0][0], d[4][0]);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const long long cell = PARITY ? c.nb[i] : c.own;
     const int slot = PARITY ? i : opp(i);
-    S* base = pop + tile_start(cell);
-    const int lane = (int)(cell & (kTile - 1));
-    float v[kF];
-#pragma unroll
-    for (int k = 0; k < kF; ++k) v[k] = d[k][i];
-#pragma unroll
-    for (int g = 0; g < 3; ++g)
-      *reinterpret_cast<V4*>(base + group_offset(slot, g, lane)) = Codec<S>::enc4(v + 4 * g, P.inv_scale + 4 * g);
-    *reinterpret_cast<V2*>(base + group_offset(slot, 3, lane)) = Codec<S>::enc2(v + 12, P.inv_scale + 12);
+    store_dir<S>(P, pop + tile_start(cell), slot, (int)(cell & (kTile - 1)), d, i,
+                 SR ? &dz : nullptr);
   }
 }
 

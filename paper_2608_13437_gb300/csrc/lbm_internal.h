@@ -30,12 +30,14 @@ cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const 
 
 // The same step with its reads staged through shared memory by bulk asynchronous copies
 // (step_staged_*.cu; variants 2, 3, 4). Only for periodic domains whose rows are whole
-// 32-cell tiles. prepare sets the kernels' shared-memory limit and returns the
+// 32-cell tiles, rounding to nearest. prepare sets the kernels' shared-memory limit and returns the
 // persistent grid size (SMs x resident blocks, at most one warp per tile). skip_first
 // is a failure-detection test hook (one warp's first copy is not issued, so its
 // bounded wait runs out and the step reports a stalled copy).
 constexpr int kFirstStagedVariant = 2, kLastStagedVariant = 4;
-inline bool staged_eligible(const DomainConst& P) { return P.bc_x == 0 && P.nx % 32 == 0; }
+inline bool staged_eligible(const DomainConst& P) {
+  return P.bc_x == 0 && P.nx % 32 == 0 && P.sround == 0;  // no stochastic rounding there
+}
 cudaError_t staged_prepare_f32(const DomainConst& P, int variant, int* grid);
 cudaError_t staged_prepare_f16(const DomainConst& P, int variant, int* grid);
 cudaError_t staged_prepare_bf16(const DomainConst& P, int variant, int* grid);

@@ -12,7 +12,7 @@ namespace lbm {
 
 static_assert(kDiagRecFloats == kDiagRecWords, "warp record size");
 
-template <int PARITY, typename S, bool HELD>
+template <int PARITY, typename S, bool HELD, bool SR>
 __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __restrict__ pop,
                                                       const float* __restrict__ ghost,
                                                       unsigned* __restrict__ flag,
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
       SensorOut so;
       collide_cell<true, true>(P, d, &so, &cd);
     }
-    store_cell<PARITY, S>(P, pop, c, d);
+    store_cell<PARITY, S, SR>(P, pop, c, d);
     diag_add_cell(P, cd, acc);
     const long long n = P.ncell;
     const long long cell = x + (long long)P.nx * (blockIdx.y + (long long)P.ny * blockIdx.z);
@@ -49,6 +49,19 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
   }
 }
 
+template <typename S, bool SR>
+void launch_step_diag_forms(const DomainConst& P, int parity, S* p, const float* ghost,
+                            unsigned* flag, float* ufield, float* rec, dim3 grid, dim3 block,
+                            cudaStream_t s) {
+  if (P.bc_x) {
+    if (parity) k_step_diag<1, S, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  } else {
+    if (parity) k_step_diag<1, S, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  }
+}
+
 template <typename S>
 cudaError_t launch_step_diag_t(const DomainConst& P, int parity, void* pop, const float* ghost,
                                unsigned* flag, float* ufield, float* rec, int block_x,
@@ -57,13 +70,13 @@ cudaError_t launch_step_diag_t(const DomainConst& P, int parity, void* pop, cons
   const dim3 block(block_x);
   const dim3 grid((P.nx + block_x - 1) / block_x, P.ny, P.nz);
   S* p = static_cast<S*>(pop);
-  if (P.bc_x) {
-    if (parity) k_step_diag<1, S, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
-    else k_step_diag<0, S, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
-  } else {
-    if (parity) k_step_diag<1, S, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
-    else k_step_diag<0, S, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  if constexpr (!std::is_same<S, float>::value) {
+    if (P.sround) {
+      launch_step_diag_forms<S, true>(P, parity, p, ghost, flag, ufield, rec, grid, block, s);
+      return cudaGetLastError();
+    }
   }
+  launch_step_diag_forms<S, false>(P, parity, p, ghost, flag, ufield, rec, grid, block, s);
   return cudaGetLastError();
 }
 

@@ -79,33 +79,26 @@ __device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __
 
 // store_cell for whole-tile rows: even steps write slot opp(i) of the own cell, odd
 // steps slot i of cell x + e_i.
-template <int PARITY, typename S>
+template <int PARITY, typename S, bool SR = false>
 __device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restrict__ pop,
                                                 const WarpTiles& T, int lane,
                                                 const float (&d)[kF][kQ]) {
-  using V4 = typename Codec<S>::V4;
-  using V2 = typename Codec<S>::V2;
+  [[maybe_unused]] Dither dz(0, 0.0f, 0.0f);
+  if constexpr (SR) dz = Dither(T.t * kTile + lane, d[0][0], d[4][0]);  // canonical index
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     long long tile = T.t;
     int ln = lane;
     if (PARITY && i > 0) link_tile(T, i, +1, lane, tile, ln);
-    const int slot = PARITY ? i : opp(i);
-    S* base = pop + tile * kTileElems;
-    float v[kF];
-#pragma unroll
-    for (int k = 0; k < kF; ++k) v[k] = d[k][i];
-#pragma unroll
-    for (int g = 0; g < 3; ++g)
-      *reinterpret_cast<V4*>(base + group_offset(slot, g, ln)) = Codec<S>::enc4(v + 4 * g, P.inv_scale + 4 * g);
-    *reinterpret_cast<V2*>(base + group_offset(slot, 3, ln)) = Codec<S>::enc2(v + 12, P.inv_scale + 12);
+    store_dir<S>(P, pop + tile * kTileElems, PARITY ? i : opp(i), ln, d, i, SR ? &dz : nullptr);
   }
 }
 
 // MINB = resident 128-thread blocks per SM the register budget is sized for:
 // 3 -> at most 170 registers (no spills), 4 -> at most 128 (a few spilled words).
 // ROWS: whole-tile rows (periodic x, nx a multiple of 32), addressed per warp.
-template <int PARITY, typename S, bool HELD, int MINB, bool ROWS>
+// SR: stochastic rounding of 16-bit storage.
+template <int PARITY, typename S, bool HELD, int MINB, bool ROWS, bool SR = false>
 __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __restrict__ pop,
                                                     const float* __restrict__ ghost,
                                                     unsigned* __restrict__ flag) {
@@ -120,7 +113,7 @@ __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __re
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
     }
-    store_cell_rows<PARITY, S>(P, pop, T, lane, d);
+    store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
   } else {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= P.nx) return;
@@ -130,23 +123,35 @@ __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __re
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
     }
-    store_cell<PARITY, S>(P, pop, c, d);
+    store_cell<PARITY, S, SR>(P, pop, c, d);
+  }
+}
+
+template <typename S, int MINB, bool SR>
+void launch_forms(const DomainConst& P, int parity, S* p, const float* ghost, unsigned* flag,
+                  dim3 grid, dim3 block, cudaStream_t s) {
+  if (P.bc_x) {
+    if (parity) k_step<1, S, true, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, true, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+  } else if (P.nx % kTile == 0) {
+    if (parity) k_step<1, S, false, MINB, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, false, MINB, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+  } else {
+    if (parity) k_step<1, S, false, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, false, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
   }
 }
 
 template <typename S, int MINB>
 void launch_variant(const DomainConst& P, int parity, S* p, const float* ghost, unsigned* flag,
                     dim3 grid, dim3 block, cudaStream_t s) {
-  if (P.bc_x) {
-    if (parity) k_step<1, S, true, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
-    else k_step<0, S, true, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
-  } else if (P.nx % kTile == 0) {
-    if (parity) k_step<1, S, false, MINB, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
-    else k_step<0, S, false, MINB, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
-  } else {
-    if (parity) k_step<1, S, false, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
-    else k_step<0, S, false, MINB, false><<<grid, block, 0, s>>>(P, p, ghost, flag);
+  if constexpr (!std::is_same<S, float>::value) {
+    if (P.sround) {
+      launch_forms<S, MINB, true>(P, parity, p, ghost, flag, grid, block, s);
+      return;
+    }
   }
+  launch_forms<S, MINB, false>(P, parity, p, ghost, flag, grid, block, s);
 }
 
 // variant 0: register budget for 3 blocks of 128 per SM; 1: for 4 blocks.

@@ -31,7 +31,8 @@ class LbmParams(ctypes.Structure):
         ("T_ref", ctypes.c_double), ("relax_in_dt", ctypes.c_int), ("sutherland", ctypes.c_int),
         ("source_mode", ctypes.c_int), ("f_mu", ctypes.c_double), ("C_sigma", ctypes.c_double),
         ("J_min", ctypes.c_double), ("omega_min", ctypes.c_double), ("sensor_mode", ctypes.c_int),
-        ("collide", ctypes.c_int), ("store", ctypes.c_int), ("use_graphs", ctypes.c_int),
+        ("collide", ctypes.c_int), ("store", ctypes.c_int), ("stochastic_round", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("pop_buffer", ctypes.c_void_p),
     ]
 

@@ -110,3 +110,17 @@ def test_every_entry_point_rejects_a_null_handle(L):
                                         "lbm_last_error", "lbm_status_string"}
     assert not untested, untested
 
+
+def test_batch_and_params_reject_invalid_stochastic_rounding(L):
+    """stochastic_round is 0 or 1, and the batched mode takes rounding to nearest only;
+    both are refused before any CUDA call."""
+    from paper_2608_13437_gb300 import inputs, lbm
+    q = dict(inputs.tgv_params(8), stochastic_round=2)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(ctypes.byref(lbm.make_params(q, "f16")), ctypes.byref(h)) == lbm.LBM_E_INVAL
+    arr = (lbm.LbmParams * 2)(lbm.make_params(inputs.tgv_params(8), "f16"),
+                              lbm.make_params(dict(inputs.tgv_params(8), stochastic_round=1), "f16"))
+    b = ctypes.c_void_p()
+    assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
+    assert b"rounds to nearest" in L.lbm_last_error()
+
