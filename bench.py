@@ -296,18 +296,19 @@ def diag_costs(torch, dom, ms_step, reps=8):
             "in_step_extra_ms": round(fused - ms_step, 4)}
 
 
-def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32"):
+def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
     per domain per step."""
     doms = inputs.batch_domains()[:n_domains]
     pl = inputs.batch_params(doms)
-    B = lbm.Batch([q for q, _ in pl], store=store)
+    B = lbm.Batch([dict(q, stochastic_round=sround) for q, _ in pl], store=store)
     ic = [[c["U0"] for _, c in pl], [c["M0"] for _, c in pl], [c["rho0"] for _, c in pl]]
     B.init_tgv(*ic)
     tune = B.autotune(4)
     cells = B.total_cells()
-    out = {"domains": len(doms), "cells": cells, "store": store, "tune": tune}
+    out = {"domains": len(doms), "cells": cells, "store": store, "stochastic_round": sround,
+           "tune": tune}
     for name, fn in (("persistent", B.step), ("sequential", B.step_sequential)):
         B.init_tgv(*ic)
         fn(warmup)
@@ -448,6 +449,8 @@ def run_gpu(args):
         variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
         variants["batch64_f16"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup,
                                             store="f16")
+        variants["batch64_f16_stochastic_rounding"] = batch_leg(
+            torch, lbm, inputs, min(args.steps, 200), args.warmup, store="f16", sround=1)
 
     cpu = cpu_baseline(n) if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank == 0:

@@ -57,7 +57,8 @@ typedef enum {
 /* Population storage. All arithmetic is FP32 in every mode.
  * F32: f - w_i Q_ref,k stored as float (the reference-shifted form of Sec. 2.2).
  * F16 / BF16: (f - w_i Q_ref,k) / s_k stored as IEEE half / bfloat16, rounded to
- * nearest even; s_k is fixed per field at init (see lbm_info). */
+ * nearest even or stochastically (lbm_params.stochastic_round); s_k is fixed per
+ * field at init (see lbm_info). */
 typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 } lbm_store;
 
 /* Element types of data exchanged with the caller. NATIVE = the stored bits
@@ -100,8 +101,10 @@ typedef struct {
   int stochastic_round;  /* 16-bit storage only: 1 rounds every stored population up or
                             down at random with the probabilities that make the rounding
                             unbiased (random bits from the cell's index and state, so the
-                            result is reproducible); 0 rounds to nearest (default). Not
-                            with the staged kernel forms or the batched mode */
+                            result is reproducible); 0 rounds to nearest (default). The
+                            staged kernel forms round to nearest only (the autotuner
+                            then chooses among the others); a batch takes one mode for
+                            all its domains */
   int use_graphs;        /* 1: lbm_step replays captured CUDA graphs of whole step pairs */
   void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
   void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
@@ -319,6 +322,22 @@ lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
  * synchronising call (lbm_synchronize, lbm_diag) returns LBM_E_CUDA, after which
  * lbm_step refuses to run until a re-init. LBM_E_INVAL for a plain form. */
 lbm_status lbm_test_skip_copy(lbm_handle* h);
+
+/* Codec test hook: the 16-bit store conversion of the step kernels (the encoding of the
+ * reference-shifted deviations of Sec. 2.2 into FP16 or BF16; no counterpart in the
+ * paper, which stores FP32) applied at unit scale to npair pairs of floats:
+ * in[2j] -> low half and in[2j+1] -> high half of out[j]. stochastic_round 0 rounds to
+ * nearest even; 1 rounds stochastically with the random word rbits[j] (its low 16 bits
+ * serve in[2j], its high 16 bits in[2j+1]; as in the kernels). store: LBM_STORE_F16 or
+ * LBM_STORE_BF16. in (2*npair floats), rbits (npair words; unused and may be NULL when
+ * rounding to nearest) and out (npair words) are DEVICE pointers owned by the caller;
+ * the work is queued on cuda_stream (a cudaStream_t, NULL for the default stream) and
+ * the call does not wait for it. LBM_E_INVAL for another store, a stochastic_round
+ * other than 0 or 1, npair outside 0..2^30 or a NULL buffer (checked before any CUDA
+ * call); LBM_E_CUDA if the launch fails. */
+lbm_status lbm_test_encode(int store, int stochastic_round, const float* in,
+                           const unsigned* rbits, unsigned* out, long long npair,
+                           void* cuda_stream);
 
 /* ---- z-slab decomposition ------------------------------------------------------ */
 

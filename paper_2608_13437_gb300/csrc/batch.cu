@@ -9,7 +9,9 @@
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
 // update is the single-domain one; domains whose rows are whole tiles use its
 // warp-uniform tile addressing. Items per warp, block size and register budget
-// come from the autotuner; the step pair is replayed from a CUDA graph.
+// come from the autotuner; the step pair is replayed from a CUDA graph. 16-bit
+// batches may round stochastically (one mode for the whole batch; a separate
+// instantiation, as for one domain).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,9 +24,9 @@
 using namespace lbm;
 
 namespace lbm {
-namespace {
+namespace batch_kernels {  // named: the host helpers below sit in an anonymous namespace
 
-template <int PARITY, int MINB, typename S>
+template <int PARITY, int MINB, typename S, bool SR>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
                                                           const int4* __restrict__ tiles,
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
         load_cell_rows<PARITY, S>(P, pop, T, lane, d);
         const float probe = collide_cell<false>(P, d, nullptr);
         if (!isfinite(probe)) atomicOr(flag, 1u);
-        store_cell_rows<PARITY, S>(P, pop, T, lane, d);
+        store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
         continue;
       }
       const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
@@ -84,14 +86,16 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
       load_cell<PARITY, false, S>(P, pop, nullptr, c, d);
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
-      store_cell<PARITY, S>(P, pop, c, d);
+      store_cell<PARITY, S, SR>(P, pop, c, d);
     }
     item = (int)__shfl_sync(0xffffffffu, claim, 0);
   }
 }
 
-}  // namespace
+}  // namespace batch_kernels
 }  // namespace lbm
+
+using lbm::batch_kernels::k_batch_step;
 
 struct lbm_batch {
   int n = 0;
@@ -102,6 +106,7 @@ struct lbm_batch {
   long long total_cells = 0;
   void* pool = nullptr;
   int store = LBM_STORE_F32;
+  bool sround = false;         // 16-bit storage rounded stochastically (all domains)
   DomainConst* d_consts = nullptr;
   void** d_pops = nullptr;
   unsigned* d_maxbits = nullptr;  // per-field maxima for the FP16 scales at init
@@ -135,35 +140,49 @@ namespace {
 
 void* domain_pop(lbm_batch* b, int d) { return static_cast<char*>(b->pool) + b->offset[d]; }
 
-template <int P, int M, typename S>
+template <int P, int M, typename S, bool SR>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(k_batch_step<P, M, S>);
+  return reinterpret_cast<void*>(k_batch_step<P, M, S, SR>);
 }
 
-template <typename S>
+template <typename S_, bool SR_>
+struct Form {
+  using S = S_;
+  static constexpr bool SR = SR_;
+};
+
+// Calls f with the Form (storage type, rounding) of the batch's kernels.
+template <typename F>
+auto with_form(const lbm_batch* b, F&& f) {
+  if (b->store == LBM_STORE_F32) return f(Form<float, false>{});
+  if (b->store == LBM_STORE_F16)
+    return b->sround ? f(Form<__half, true>{}) : f(Form<__half, false>{});
+  return b->sround ? f(Form<__nv_bfloat16, true>{}) : f(Form<__nv_bfloat16, false>{});
+}
+
+template <typename S, bool SR>
 cudaError_t set_smem(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<0, 3, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 3, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<0, 4, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 4, S>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<0, 3, S, SR>(), attr, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 3, S, SR>(), attr, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<0, 4, S, SR>(), attr, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 4, S, SR>(), attr, (int)smem);
   return e;
-}
-
-template <typename S>
-void* any_kernel(int variant) {
-  return variant ? kernel_ptr<0, 4, S>() : kernel_ptr<0, 3, S>();
 }
 
 // Grid size for the current block size and register budget: every block resident.
 lbm_status size_grid(lbm_batch* b) {
   int per_sm = 0;
-  void* fn = b->store == LBM_STORE_F32 ? any_kernel<float>(b->variant)
-             : b->store == LBM_STORE_F16 ? any_kernel<__half>(b->variant)
-                                         : any_kernel<__nv_bfloat16>(b->variant);
+  void* fn = with_form(b, [&](auto f) {
+    using F = decltype(f);
+    return b->variant ? kernel_ptr<0, 4, typename F::S, F::SR>()
+                      : kernel_ptr<0, 3, typename F::S, F::SR>();
+  });
   if (b->smem > 48 * 1024) {
-    cudaError_t e = b->store == LBM_STORE_F32 ? set_smem<float>(b->smem)
-                    : b->store == LBM_STORE_F16 ? set_smem<__half>(b->smem)
-                                                : set_smem<__nv_bfloat16>(b->smem);
+    cudaError_t e = with_form(b, [&](auto f) {
+      using F = decltype(f);
+      return set_smem<typename F::S, F::SR>(b->smem);
+    });
     LBM_CUDA(e);
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, b->smem);
@@ -178,25 +197,31 @@ lbm_status size_grid(lbm_batch* b) {
   return LBM_OK;
 }
 
-template <typename S>
+template <typename S, bool SR>
 void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
   const dim3 g(b->grid), bl(b->block);
+#define LBM_BATCH_LAUNCH(PAR, MB)                                                           \
+  k_batch_step<PAR, MB, S, SR><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, \
+                                                      b->n, b->total_tiles,                 \
+                                                      b->tiles_per_item, b->d_counter, b->flag)
   if (b->variant) {
-    if (parity) k_batch_step<1, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 4, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    if (parity) LBM_BATCH_LAUNCH(1, 4);
+    else LBM_BATCH_LAUNCH(0, 4);
   } else {
-    if (parity) k_batch_step<1, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
-    else k_batch_step<0, 3, S><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, b->n, b->total_tiles, b->tiles_per_item, b->d_counter, b->flag);
+    if (parity) LBM_BATCH_LAUNCH(1, 3);
+    else LBM_BATCH_LAUNCH(0, 3);
   }
+#undef LBM_BATCH_LAUNCH
 }
 
 // One persistent launch: zero the work-item counter, then the kernel.
 cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if (b->store == LBM_STORE_F32) launch_typed<float>(b, parity, s);
-  else if (b->store == LBM_STORE_F16) launch_typed<__half>(b, parity, s);
-  else launch_typed<__nv_bfloat16>(b, parity, s);
+  with_form(b, [&](auto f) {
+    using F = decltype(f);
+    launch_typed<typename F::S, F::SR>(b, parity, s);
+  });
   return cudaGetLastError();
 }
 
@@ -239,6 +264,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   if (!b) return fail(LBM_E_NOMEM, "host allocation failed");
   b->n = n;
   b->store = params[0].store;
+  b->sround = params[0].stochastic_round != 0 && params[0].store != LBM_STORE_F32;
   size_t bytes = 0;
   for (int d = 0; d < n; ++d) {
     lbm_status s = validate(&params[d]);
@@ -250,9 +276,9 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
     }
-    if (params[d].stochastic_round != 0) {
+    if (params[d].stochastic_round != params[0].stochastic_round) {
       delete b;
-      return fail(LBM_E_INVAL, "domain %d: the batched mode rounds to nearest (stochastic_round = 0)", d);
+      return fail(LBM_E_INVAL, "domain %d: the batched mode takes one rounding mode (stochastic_round)", d);
     }
     b->prm.push_back(params[d]);
     double dt, tR, tq;

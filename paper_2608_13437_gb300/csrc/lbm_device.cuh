@@ -106,16 +106,13 @@ struct Codec16 {
     if (!kScaled) return from_f2(i[0], i[1]);
     return from_f2(i[0] * is[0], i[1] * is[1]);
   }
-  // Stochastic rounding: the float's bits below the 16-bit format's last place (13 for
-  // FP16, 16 for BF16) get a random addend before they are cut off, so a value is
-  // rounded away from zero with probability equal to its distance from the value
-  // below; the cut value is exact in the 16-bit format (normal range), so the
-  // conversion that follows changes nothing. r supplies the addend in its low bits.
-  static constexpr int kCut = kScaled ? 13 : 16;
-  static __device__ __forceinline__ float sr_cut(float x, unsigned r) {
-    constexpr unsigned mask = (1u << kCut) - 1u;
-    return __uint_as_float((__float_as_uint(x) + (r & mask)) & ~mask);
-  }
+  // Stochastic rounding of a pair (a to the low half, b to the high half): the
+  // hardware conversion with random bits (cvt.rs, sm_100 and later) adds the low 16
+  // bits of r below a's last kept place (FP16 uses 13 of them, BF16 all 16), the high
+  // 16 bits below b's, and cuts what lies below. A value rounds away from zero with
+  // probability equal to its distance from the value below, in ulps; FP16 subnormals
+  // included.
+  static __device__ __forceinline__ unsigned from_f2_sr(float a, float b, unsigned r);
   static __device__ __forceinline__ V4 enc4_sr(const float i[4], const float* is, unsigned r0,
                                                unsigned r1) {
     float a = i[0], b = i[1], c = i[2], e = i[3];
@@ -125,8 +122,7 @@ struct Codec16 {
       c = c * is[2];
       e = e * is[3];
     }
-    return make_uint2(from_f2(sr_cut(a, r0), sr_cut(b, r0 >> 16)),
-                      from_f2(sr_cut(c, r1), sr_cut(e, r1 >> 16)));
+    return make_uint2(from_f2_sr(a, b, r0), from_f2_sr(c, e, r1));
   }
   static __device__ __forceinline__ V2 enc2_sr(const float i[2], const float* is, unsigned r) {
     float a = i[0], b = i[1];
@@ -134,7 +130,7 @@ struct Codec16 {
       a = a * is[0];
       b = b * is[1];
     }
-    return from_f2(sr_cut(a, r), sr_cut(b, r >> 16));
+    return from_f2_sr(a, b, r);
   }
 };
 
@@ -152,6 +148,13 @@ __device__ __forceinline__ unsigned Codec16<__half, __half2, true>::from_f2(floa
   return w;
 }
 template <>
+__device__ __forceinline__ unsigned Codec16<__half, __half2, true>::from_f2_sr(float a, float b,
+                                                                               unsigned r) {
+  unsigned w;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(b), "f"(a), "r"(r));
+  return w;
+}
+template <>
 __device__ __forceinline__ float2 Codec16<__nv_bfloat16, __nv_bfloat162, false>::to_f2(unsigned w) {
   __nv_bfloat162 h;
   memcpy(&h, &w, 4);
@@ -162,6 +165,13 @@ __device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162, false
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   unsigned w;
   memcpy(&w, &h, 4);
+  return w;
+}
+template <>
+__device__ __forceinline__ unsigned Codec16<__nv_bfloat16, __nv_bfloat162, false>::from_f2_sr(
+    float a, float b, unsigned r) {
+  unsigned w;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(b), "f"(a), "r"(r));
   return w;
 }
 
@@ -298,10 +308,13 @@ __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restr
   }
 }
 
-// Random words for stochastic rounding, one stream per cell and step: seeded from the
-// cell's index and the bits of two of its post-collision populations (so the stream
-// changes as the state evolves, and every kernel form draws the same words for the
-// same cell), then advanced by Marsaglia's xorshift32.
+// Random words for stochastic rounding, one stream per cell and step: the seed mixes
+// the cell's index with the bits of two of its post-collision populations (so the
+// stream changes as the state evolves, and every kernel form draws the same words for
+// the same cell) through a multiply-xorshift hash; the words are then a Weyl sequence
+// (seed + k times the golden-ratio constant), one addition each. Every word is uniform
+// because the seed is, so every rounding is unbiased; words of one cell differ by
+// fixed offsets, which correlates roundings within a cell but biases none.
 struct Dither {
   unsigned s;
   __device__ __forceinline__ Dither(long long cell, float a, float b) {
@@ -311,12 +324,12 @@ struct Dither {
     x ^= x >> 15;
     x *= 0x2C1B3C6Du;
     x ^= x >> 13;
-    s = x | 1u;  // xorshift32 needs a non-zero state
+    x *= 0x297A2D39u;
+    x ^= x >> 16;
+    s = x;
   }
   __device__ __forceinline__ unsigned next() {
-    s ^= s << 13;
-    s ^= s >> 17;
-    s ^= s << 5;
+    s += 0x9E3779B9u;
     return s;
   }
 };

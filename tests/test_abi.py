@@ -97,6 +97,7 @@ def test_every_entry_point_rejects_a_null_handle(L):
         "lbm_batch_step_sequential": (V, 1), "lbm_batch_synchronize": (V,),
         "lbm_batch_moments": (V, 0, 0, buf, 0, 0), "lbm_batch_info": (V, V, 0, V),
         "lbm_batch_autotune": (V, 1, V, V, V),
+        "lbm_test_encode": (1, 0, V, V, V, 4, V),
     }
     for name, args in calls.items():
         fn = getattr(L, name)
@@ -111,9 +112,21 @@ def test_every_entry_point_rejects_a_null_handle(L):
     assert not untested, untested
 
 
+def test_encode_hook_validates_before_any_cuda_call(L):
+    """lbm_test_encode refuses FP32 storage, a bad rounding mode, a bad count and NULL
+    buffers with LBM_E_INVAL; zero pairs is a no-op."""
+    from paper_2608_13437_gb300 import lbm
+    buf = ctypes.create_string_buffer(64)
+    assert L.lbm_test_encode(0, 0, buf, buf, buf, 4, None) == lbm.LBM_E_INVAL
+    assert L.lbm_test_encode(1, 2, buf, buf, buf, 4, None) == lbm.LBM_E_INVAL
+    assert L.lbm_test_encode(2, 0, buf, buf, buf, -1, None) == lbm.LBM_E_INVAL
+    assert L.lbm_test_encode(1, 1, buf, None, buf, 4, None) == lbm.LBM_E_INVAL
+    assert L.lbm_test_encode(1, 1, None, None, None, 0, None) == lbm.LBM_OK
+
+
 def test_batch_and_params_reject_invalid_stochastic_rounding(L):
-    """stochastic_round is 0 or 1, and the batched mode takes rounding to nearest only;
-    both are refused before any CUDA call."""
+    """stochastic_round is 0 or 1, and a batch takes one rounding mode for all its
+    domains; both are refused before any CUDA call."""
     from paper_2608_13437_gb300 import inputs, lbm
     q = dict(inputs.tgv_params(8), stochastic_round=2)
     h = ctypes.c_void_p()
@@ -122,5 +135,5 @@ def test_batch_and_params_reject_invalid_stochastic_rounding(L):
                               lbm.make_params(dict(inputs.tgv_params(8), stochastic_round=1), "f16"))
     b = ctypes.c_void_p()
     assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
-    assert b"rounds to nearest" in L.lbm_last_error()
+    assert b"one rounding mode" in L.lbm_last_error()
 

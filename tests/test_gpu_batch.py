@@ -105,12 +105,13 @@ def test_full_64_domain_batch_stays_finite_and_conserves(lbm, oracle_mod):
     B.close()
 
 
-@pytest.mark.parametrize("store", ["f16", "bf16"])
-def test_reduced_storage_batch_matches_single_domains(lbm, store):
-    """A batch in 16-bit storage: persistent and per-domain launches agree bit for
-    bit, and each domain equals a single-domain run of it (same scales, same
-    arithmetic)."""
+@pytest.mark.parametrize("store,sr", [("f16", 0), ("bf16", 0), ("f16", 1), ("bf16", 1)])
+def test_reduced_storage_batch_matches_single_domains(lbm, store, sr):
+    """A batch in 16-bit storage, rounded to nearest or stochastically: persistent
+    and per-domain launches agree bit for bit, and each domain equals a single-domain
+    run of it (same scales, same arithmetic, same random bits per cell)."""
     params, ic = _small_batch()
+    params = [dict(q, stochastic_round=sr) for q in params]
     a = lbm.Batch(params, store=store)
     b = lbm.Batch(params, store=store)
     for B in (a, b):

@@ -162,7 +162,7 @@ def test_sod_matches_oracle_and_exact(lbm, oracle_mod, store, sr, mean_bound, ma
     the oracle's and of the exact solution; density profile close to the oracle's;
     total mass kept. Observed (mean |d rho| / mass drift): FP32 1.1e-5 / 1e-6; FP16
     1.2e-2 / +1.9e-2 and BF16 1.7e-2 / -2.8e-2 rounding to nearest at omega = 2; with
-    stochastic rounding FP16 1.6e-3 / 2.3e-4 and BF16 3.7e-3 / 7.7e-4."""
+    stochastic rounding FP16 1.6e-3 / 8.3e-5 and BF16 3.5e-3 / 8.6e-4."""
     from oracle import riemann
     n = 1024
     p = inputs.sod_params(n)
@@ -422,6 +422,81 @@ def test_staged_copy_wait_runs_out_and_is_reported(lbm):
     assert np.array_equal(d.populations("native").view(np.uint32), ref.populations("native").view(np.uint32))
     d.close()
     ref.close()
+
+
+def _random_floats(rng, n, e_lo, e_hi):
+    """n float32 values of random sign and mantissa, binary exponents e_lo..e_hi."""
+    e = rng.integers(127 + e_lo, 127 + e_hi + 1, n, dtype=np.uint32)
+    u = (rng.integers(0, 2, n, dtype=np.uint32) << 31) | (e << 23) | rng.integers(0, 1 << 23, n, dtype=np.uint32)
+    return u.view(np.float32)
+
+
+def _cut(x, r, bits):
+    """The stochastic-rounding rule: add r's low `bits` bits below the kept part of
+    the float's significand, then drop those bits (toward zero)."""
+    m = np.uint32((1 << bits) - 1)
+    return ((x.view(np.uint32) + (r & m)) & ~m).view(np.float32)
+
+
+def _bf16_rne(x):
+    """FP32 -> BF16 bits rounded to nearest even (finite inputs): add 0x7FFF plus the
+    lowest kept bit, then drop 16 bits."""
+    u = x.view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint32)
+
+
+def _f16_bits(x):
+    return x.astype(np.float16).view(np.uint16).astype(np.uint32)
+
+
+@pytest.mark.parametrize("store", ["f16", "bf16"])
+def test_store_codec_matches_rounding_definitions(lbm, store):
+    """The step kernels' 16-bit store conversion (lbm_test_encode) against definitions
+    written here: round to nearest even (numpy's FP16 cast; the integer rule for BF16)
+    and stochastic rounding (the random word's 16 bits, FP16: the low 13 of them, added
+    below the last kept place, then cut), bit for bit, on random values of both signs
+    over the format's normal range (FP16: its subnormals too when rounding to nearest).
+    A pair's first value takes the word's low half, the second its high half. FP16
+    subnormals round stochastically to a neighbouring subnormal, without bias."""
+    import torch
+    rng = np.random.default_rng(20261203)
+    n = 1 << 18
+    if store == "f16":
+        x = np.concatenate([_random_floats(rng, n, -14, 14), _random_floats(rng, n // 4, -26, -15),
+                            np.array([0.0, -0.0, 65504.0, -65504.0], np.float32)])
+        rn_ref = _f16_bits(x)
+    else:
+        x = np.concatenate([_random_floats(rng, n, -100, 100), np.array([0.0, -0.0], np.float32)])
+        rn_ref = _bf16_rne(x)
+    x = x[: x.size // 2 * 2]
+    rn_ref = rn_ref[: x.size]
+    dev = torch.from_numpy(x).cuda()
+    got = lbm.encode_pairs(store, dev).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got & 0xFFFF, rn_ref[0::2]) and np.array_equal(got >> 16, rn_ref[1::2])
+    # stochastic: normal-range values only for the bit-exact rule
+    if store == "f16":
+        x = _random_floats(rng, n, -14, 14)
+        bits, conv = 13, _f16_bits
+    else:
+        x = _random_floats(rng, n, -100, 100)
+        bits, conv = 16, lambda v: v.view(np.uint32) >> 16
+    r = rng.integers(0, 1 << 32, n // 2, dtype=np.uint32)
+    got = lbm.encode_pairs(store, torch.from_numpy(x).cuda(),
+                           torch.from_numpy(r.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got & 0xFFFF, conv(_cut(x[0::2], r, bits)))
+    assert np.array_equal(got >> 16, conv(_cut(x[1::2], r >> 16, bits)))
+    assert not np.array_equal(got & 0xFFFF, (_f16_bits(x) if store == "f16" else _bf16_rne(x))[0::2])
+    if store == "f16":  # subnormal: each result a neighbour on the 2^-24 grid, mean unbiased
+        k = 1 << 16
+        v = np.full(2 * k, 1e-6, np.float32)  # 16.777... units of 2^-24
+        r = rng.integers(0, 1 << 32, k, dtype=np.uint32)
+        got = lbm.encode_pairs(store, torch.from_numpy(v).cuda(),
+                               torch.from_numpy(r.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+        h = np.concatenate([got & 0xFFFF, got >> 16]).astype(np.uint16).view(np.float16).astype(np.float64)
+        q = h / 2.0 ** -24
+        assert set(np.unique(q)) <= {16.0, 17.0}
+        f = float(np.float32(1e-6)) / 2.0 ** -24 - 16.0
+        assert abs(q.mean() - 16.0 - f) < 5 * np.sqrt(f * (1 - f) / q.size)
 
 
 @pytest.mark.parametrize("store", ["f16", "bf16"])
