@@ -92,6 +92,7 @@ _SIGNATURES = {
     "lbm_diag_static": (_IP, [_VP, ctypes.POINTER(LbmDiag)]),
     "lbm_step_diag": (_IP, [_VP, _IP, ctypes.POINTER(LbmDiag)]),
     "lbm_test_skip_copy": (_IP, [_VP]),
+    "lbm_test_encode": (_IP, [_IP, _IP, _VP, _VP, _VP, ctypes.c_longlong, _VP]),
     "lbm_plane_get": (_IP, [_VP, _IP, _IP, _VP, _IP]),
     "lbm_plane_set": (_IP, [_VP, _IP, _IP, _VP, _IP]),
     "lbm_populations_get": (_IP, [_VP, _VP, _IP, _IP]),
@@ -422,3 +423,26 @@ class Batch:
         check(lib().lbm_batch_autotune(self._h, int(steps_per_trial), ctypes.byref(tc),
                                        ctypes.byref(bt), ctypes.byref(ms)))
         return {"tile_cells": tc.value, "block": bt.value, "ms_per_step": ms.value}
+
+
+def encode_pairs(store, values, rbits=None):
+    """lbm_test_encode on device tensors: values (float32, 2 n elements), rbits (n
+    32-bit words as int32, or None to round to nearest) -> n packed words (int32)."""
+    import torch
+    v = values.contiguous()
+    if v.dtype != torch.float32 or not v.is_cuda or v.numel() % 2:
+        raise ValueError("values must be a CUDA float32 tensor of even length")
+    n = v.numel() // 2
+    out = torch.empty(n, dtype=torch.int32, device=v.device)
+    r = None
+    if rbits is not None:
+        r = rbits.contiguous()
+        if r.dtype != torch.int32 or r.numel() != n or r.device != v.device:
+            raise ValueError("rbits must be an int32 tensor of one word per pair on the same device")
+    stream = torch.cuda.current_stream(v.device)
+    check(lib().lbm_test_encode(STORES[store] if isinstance(store, str) else int(store),
+                                int(r is not None), v.data_ptr(),
+                                r.data_ptr() if r is not None else None, out.data_ptr(), n,
+                                stream.cuda_stream))
+    stream.synchronize()
+    return out
