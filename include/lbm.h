@@ -24,8 +24,12 @@
  *     population arrays are [k][i][z][y][x] in canonical order: the pre-collision
  *     populations of the current time step, independent of the in-place storage.
  *   - "dst_on_device"/"src_on_device" = 1: the pointer is device memory on the
- *     handle's device; 0: host memory (pageable or pinned). The caller owns every
- *     buffer it passes in; the library owns the device memory it allocates.
+ *     handle's device; 0: host memory (pageable or pinned). lbm_init_fields,
+ *     lbm_init_state, lbm_moments and lbm_sensor read or write page-locked host
+ *     memory (cudaHostAlloc, cudaHostRegister; element-aligned) directly from their
+ *     kernels over the CPU-GPU link; pageable memory goes through a device staging
+ *     buffer. The caller owns every buffer it passes in; the library owns the device
+ *     memory it allocates.
  *   - Work is issued on the handle's CUDA stream (borrowed from the caller, or the
  *     legacy default stream when none is given). Calls that return data to the
  *     host synchronise that stream; lbm_step does not.

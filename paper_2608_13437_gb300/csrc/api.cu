@@ -476,6 +476,23 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
   return run_init(h, sp);
 }
 
+// Page-locked host memory (cudaHostAlloc, cudaHostRegister) is mapped into the GPU's
+// address space, so kernels read and write it directly over the CPU-GPU link
+// (NVLink-C2C between Grace and the GPU): host inputs and outputs in such memory need
+// no device staging buffer and no separate copy. Returns the device address of a
+// page-locked buffer, or nullptr for pageable memory and for a pointer that is not a
+// multiple of `align` (those take the staged path).
+static void* mapped_host(const void* p, size_t align) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  if (reinterpret_cast<uintptr_t>(a.devicePointer) % align) return nullptr;
+  return a.devicePointer;
+}
+
 static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype,
                                    int kind, int nfield) {
   Range range_("lbm_init_fields");
@@ -484,7 +501,10 @@ static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on
   const size_t bytes = (size_t)nfield * h->ncell * (dtype == LBM_DT_F64 ? 8 : 4);
   void* dev = const_cast<void*>(fields);
   void* tmp = nullptr;
-  if (!src_on_device) {
+  void* mapped = src_on_device ? nullptr : mapped_host(fields, dtype == LBM_DT_F64 ? 8 : 4);
+  if (mapped) {
+    dev = mapped;  // page-locked: the kernels read it directly
+  } else if (!src_on_device) {
     if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
       cudaGetLastError();
       return fail(LBM_E_NOMEM, "cudaMalloc of %zu staging bytes failed", bytes);
@@ -604,6 +624,13 @@ lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, i
                             dtype == LBM_DT_F64, 0, h->ncell, h->stream));
     return LBM_OK;
   }
+  if (void* m = mapped_host(dst, es)) {  // page-locked: the kernel writes it directly
+    cudaError_t e = launch_moments(h->P, h->prm.store, parity, h->pop, h->ghost, which, m,
+                                   dtype == LBM_DT_F64, 0, h->ncell, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_E_CUDA, "moments failed: %s", cudaGetErrorString(e));
+    return LBM_OK;
+  }
   long long chunk = (long long)(kStageBytes / (es * nf));
   if (chunk > h->ncell) chunk = h->ncell;
   lbm_status st = ensure_stage(h);
@@ -632,6 +659,13 @@ lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
   if (dst_on_device) {
     LBM_CUDA(launch_sensor(h->P, h->prm.store, parity, h->pop, h->ghost, dst, dtype == LBM_DT_F64, 0,
                            h->ncell, h->stream));
+    return LBM_OK;
+  }
+  if (void* m = mapped_host(dst, es)) {  // page-locked: the kernel writes it directly
+    cudaError_t e = launch_sensor(h->P, h->prm.store, parity, h->pop, h->ghost, m,
+                                  dtype == LBM_DT_F64, 0, h->ncell, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_E_CUDA, "sensor failed: %s", cudaGetErrorString(e));
     return LBM_OK;
   }
   long long chunk = (long long)(kStageBytes / (es * 3));
