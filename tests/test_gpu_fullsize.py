@@ -3,6 +3,8 @@
     cone: after n steps a cell depends only on cells within n lattice steps, so the
     oracle recomputes a (B + 2n)^3 window of the same initial field and its central
     B^3 cells must match the GPU's (sampled outputs at full size);
+  * the largest FP32 cube that fits (840^3) on light cones, interior and across the
+    periodic corner;
   * 512^3: the TMA-staged step form against the plain kernel (bit for bit, on the
     device) and the in-step diagnostics against the separate pass;
   * dissipation time series per storage type against the oracle (64^3, 400 steps);
@@ -62,6 +64,47 @@ def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps):
     r = o.primitives()[:, steps:steps + B, steps:steps + B, steps:steps + B]
     errs = {"rho": rel_l2(g[0], r[0]), "u": rel_l2(g[1:4], r[1:4]), "T": rel_l2(g[4], r[4])}
     assert max(errs.values()) < 1e-5, errs
+
+
+def test_largest_fp32_domain_matches_oracle_on_light_cones(lbm, oracle_mod):
+    """The largest cube whose FP32 populations (392 B per cell, 216 GiB at 840^3:
+    593 M cells, 5.8e10 stored values) and a primitive readback fit on the GPU with a
+    margin: after 9 steps, windows in the interior and across the periodic corner
+    (the highest cell indices, wrapping to the lowest) match the oracle's light-cone
+    recomputation at the FP32 tolerance. Skipped when the free device memory is
+    short."""
+    import torch
+    n, B, steps = 840, 10, 9
+    torch.cuda.empty_cache()
+    need = n ** 3 * (392 + 6 * 4) + (8 << 30)
+    free, _ = torch.cuda.mem_get_info()
+    if free < need:
+        pytest.skip(f"needs {need / 2**30:.0f} GiB free, {free / 2**30:.0f} GiB available")
+    p = inputs.tgv_params(n)
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.step(steps)
+    dom.synchronize()
+    prim = dom.moments_device(lbm.MOM_PRIM)
+    origins = [(400, 123, 777), (n - 4, n - 6, n - 3)]  # interior; across the corner
+    got = []
+    for x0, y0, z0 in origins:
+        ix, iy, iz = [torch.arange(o, o + B, device=prim.device) % n for o in (x0, y0, z0)]
+        w = prim.index_select(3, ix).index_select(2, iy).index_select(1, iz)
+        got.append(w.double().cpu().numpy())
+    del prim
+    dom.close()
+    torch.cuda.empty_cache()
+    side = B + 2 * steps
+    q = dict(p)
+    q.update(nx=side, ny=side, nz=side)
+    for (x0, y0, z0), g in zip(origins, got):
+        o = make_oracle(q)
+        o.init_tgv(1.0, 1.25, 1.0, gn=n, origin=(x0 - steps, y0 - steps, z0 - steps))
+        o.step(steps)
+        r = o.primitives()[:, steps:steps + B, steps:steps + B, steps:steps + B]
+        errs = {"rho": rel_l2(g[0], r[0]), "u": rel_l2(g[1:4], r[1:4]), "T": rel_l2(g[4], r[4])}
+        assert max(errs.values()) < 1e-5, ((x0, y0, z0), errs)
 
 
 def test_512_staged_form_and_in_step_diagnostics(lbm):
