@@ -4,7 +4,7 @@
 // stages every domain's constants in shared memory once; then each warp claims
 // items from a counter, an item being `tiles_per_item` consecutive 32-cell layout
 // tiles, until none are left. A tile's domain and the (x, y, z) of its first cell
-// come from a per-tile table (one 16-byte broadcast load instead of a search and
+// come from a per-tile table (one 8-byte record per tile instead of a search and
 // two divisions); no block-wide synchronisation happens after
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
 // update is the single-domain one; domains whose rows are whole tiles use its
@@ -29,7 +29,7 @@ namespace batch_kernels {  // named: the host helpers below sit in an anonymous 
 template <int PARITY, int MINB, typename S, bool SR>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
-                                                          const int4* __restrict__ tiles,
+                                                          const uint2* __restrict__ tiles,
                                                           int ndom, int total_tiles,
                                                           int tiles_per_item,
                                                           unsigned* __restrict__ next_item,
@@ -49,15 +49,27 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
   const int n_items = (total_tiles + tiles_per_item - 1) / tiles_per_item;
   // Items are claimed in order from one counter (zeroed before the launch), so the
   // tiles in flight stay a compact window of the buffer, as with hardware block
-  // scheduling. The next claim is issued before the current item is processed.
+  // scheduling. An item's tile records are loaded at once, one per lane (items hold at
+  // most 32 tiles), and handed to the tiles by shuffles, so only an item's first tile
+  // waits for a record load; the next item is claimed when the current one starts.
+  auto records = [&](int it) {
+    const int t = it * tiles_per_item + lane;
+    return (it < n_items && lane < tiles_per_item && t < total_tiles) ? __ldg(&tiles[t])
+                                                                      : make_uint2(0u, 0u);
+  };
   unsigned claim = 0;
   if (lane == 0) claim = atomicAdd(next_item, 1u);
   int item = (int)__shfl_sync(0xffffffffu, claim, 0);
   while (item < n_items) {
     if (lane == 0) claim = atomicAdd(next_item, 1u);
-    const int t_end = min(total_tiles, (item + 1) * tiles_per_item);
-    for (int t = item * tiles_per_item; t < t_end; ++t) {
-      const int4 ti = __ldg(&tiles[t]);  // domain, x0, y0, z0 of the tile's first cell
+    const uint2 rec = records(item);
+    const int count = min(tiles_per_item, total_tiles - item * tiles_per_item);
+    for (int j = 0; j < count; ++j) {
+      // the tile's record: domain | x0 << 16, y0 | z0 << 16 (its first cell)
+      const unsigned r0 = __shfl_sync(0xffffffffu, rec.x, j);
+      const unsigned r1 = __shfl_sync(0xffffffffu, rec.y, j);
+      const int4 ti = make_int4((int)(r0 & 0xFFFFu), (int)(r0 >> 16), (int)(r1 & 0xFFFFu),
+                                (int)(r1 >> 16));
       const int lo = ti.x;
       const DomainConst& P = sP[lo];
       S* pop = sPop[lo];
@@ -69,24 +81,25 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
         const float probe = collide_cell<false>(P, d, nullptr);
         if (!isfinite(probe)) atomicOr(flag, 1u);
         store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
-        continue;
-      }
-      const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
-      if (first + lane >= P.ncell) continue;
-      // this lane's (x, y, z): carry x past the row end (several rows when nx < 32)
-      int x = ti.y + lane, y = ti.z, z = ti.w;
-      while (x >= P.nx) {
-        x -= P.nx;
-        if (++y == P.ny) {
-          y = 0;
-          ++z;
+      } else {
+        const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
+        if (first + lane < P.ncell) {
+          // this lane's (x, y, z): carry x past the row end (several rows when nx < 32)
+          int x = ti.y + lane, y = ti.z, z = ti.w;
+          while (x >= P.nx) {
+            x -= P.nx;
+            if (++y == P.ny) {
+              y = 0;
+              ++z;
+            }
+          }
+          const CellIndex c = make_index(P, x, y, z);
+          load_cell<PARITY, false, S>(P, pop, nullptr, c, d);
+          const float probe = collide_cell<false>(P, d, nullptr);
+          if (!isfinite(probe)) atomicOr(flag, 1u);
+          store_cell<PARITY, S, SR>(P, pop, c, d);
         }
       }
-      const CellIndex c = make_index(P, x, y, z);
-      load_cell<PARITY, false, S>(P, pop, nullptr, c, d);
-      const float probe = collide_cell<false>(P, d, nullptr);
-      if (!isfinite(probe)) atomicOr(flag, 1u);
-      store_cell<PARITY, S, SR>(P, pop, c, d);
     }
     item = (int)__shfl_sync(0xffffffffu, claim, 0);
   }
@@ -110,7 +123,7 @@ struct lbm_batch {
   DomainConst* d_consts = nullptr;
   void** d_pops = nullptr;
   unsigned* d_maxbits = nullptr;  // per-field maxima for the FP16 scales at init
-  int4* d_tiles = nullptr;     // per tile: domain and (x, y, z) of its first cell
+  uint2* d_tiles = nullptr;    // per tile: domain | x << 16, y | z << 16 of its first cell
   unsigned* d_counter = nullptr;  // work-item counter of the persistent kernel
   int total_tiles = 0;
   int tiles_per_item = 4;      // layout tiles a warp takes at a time
@@ -260,6 +273,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   if (!out) return fail(LBM_E_INVAL, "out is NULL");
   *out = nullptr;
   if (n < 1 || !params) return fail(LBM_E_INVAL, "need n >= 1 domains");
+  if (n > 65535) return fail(LBM_E_INVAL, "at most 65535 domains in one batch");
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return fail(LBM_E_NOMEM, "host allocation failed");
   b->n = n;
@@ -275,6 +289,10 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     if (params[d].bc_x != 0 || params[d].store != params[0].store) {
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
+    }
+    if (params[d].nx > 65535) {  // tile records hold 16-bit coordinates
+      delete b;
+      return fail(LBM_E_INVAL, "domain %d: the batched mode takes nx <= 65535", d);
     }
     if (params[d].stochastic_round != params[0].stochastic_round) {
       delete b;
@@ -311,27 +329,28 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   for (int d = 0; d < n; ++d) prefix[d + 1] = prefix[d] + (int)b->P[d].ntile;
   b->total_tiles = prefix[n];
   b->smem = sizeof(DomainConst) * n + sizeof(void*) * n;
-  std::vector<int4> tiles((size_t)b->total_tiles);
+  std::vector<uint2> tiles((size_t)b->total_tiles);
   for (int d = 0; d < n; ++d) {
     const DomainConst& P = b->P[d];
     for (long long j = 0; j < P.ntile; ++j) {
       const long long first = j * kTile;
-      tiles[(size_t)prefix[d] + j] = make_int4(d, (int)(first % P.nx), (int)((first / P.nx) % P.ny),
-                                               (int)(first / ((long long)P.nx * P.ny)));
+      const unsigned x0 = (unsigned)(first % P.nx), y0 = (unsigned)((first / P.nx) % P.ny);
+      const unsigned z0 = (unsigned)(first / ((long long)P.nx * P.ny));
+      tiles[(size_t)prefix[d] + j] = make_uint2((unsigned)d | (x0 << 16), y0 | (z0 << 16));
     }
   }
   if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pops, sizeof(void*) * n) != cudaSuccess ||
       cudaMalloc(&b->d_maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_tiles, sizeof(uint2) * tiles.size()) != cudaSuccess ||
       cudaMalloc(&b->d_counter, 64) != cudaSuccess ||
       cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
   }
   if (cudaMemcpy(b->d_pops, ptrs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tiles, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "batch table upload failed"));
   lbm_status s = upload_consts(b);
@@ -510,7 +529,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells
   if (!b->initialized) return fail(LBM_E_STATE, "autotune needs an initialised batch");
   if (steps_per_trial < 2) steps_per_trial = 8;
   steps_per_trial += steps_per_trial & 1;  // whole pairs keep the parity
-  const int items[] = {1, 2, 4, 8};
+  const int items[] = {1, 2, 4, 8, 16, 32};  // at most 32: one tile record per lane
   const int blocks[] = {64, 128};
   const int variants[] = {0, 1};
   cudaEvent_t a, e;
