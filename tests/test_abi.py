@@ -137,3 +137,21 @@ def test_batch_and_params_reject_invalid_stochastic_rounding(L):
     assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
     assert b"one rounding mode" in L.lbm_last_error()
 
+
+
+def test_batch_rejects_more_domains_or_wider_rows_than_its_tile_records_hold(L):
+    """The batched kernel's per-tile records hold 16-bit domain indices and
+    coordinates: a batch of more than 65535 domains, or a domain with nx > 65535, is
+    refused before any CUDA call."""
+    from paper_2608_13437_gb300 import inputs, lbm
+    one = (lbm.LbmParams * 1)(lbm.make_params(inputs.tgv_params(8), "f32"))
+    b = ctypes.c_void_p()
+    assert L.lbm_batch_create(65536, one, ctypes.byref(b)) == lbm.LBM_E_INVAL
+    assert not b.value
+    assert b"65535 domains" in L.lbm_last_error()
+    wide = dict(inputs.tgv_params(8), nx=65536, ny=1, nz=1)
+    arr = (lbm.LbmParams * 2)(lbm.make_params(inputs.tgv_params(8), "f32"),
+                              lbm.make_params(wide, "f32"))
+    assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
+    assert not b.value
+    assert b"nx <= 65535" in L.lbm_last_error()
