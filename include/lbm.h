@@ -133,6 +133,8 @@ typedef struct {
                                memory by bulk asynchronous copies, a persistent grid of
                                4-warp blocks: 2 stages per warp with <= 170 registers (2),
                                2 stages with <= 128 (3), 3 stages with <= 170 (4) */
+  int prefetch_tiles;       /* L2 prefetch distance of variants 0 and 1 on whole-tile rows
+                               (see lbm_set_prefetch); 0 = off */
 } lbm_info_t;
 
 /* Diagnostics (Sec. 3.2, Eq. 7). Sums and extrema in FP64 over all cells.
@@ -156,6 +158,7 @@ typedef struct {
   int variant;          /* register budget (see lbm_info_t) */
   float ms_per_step;    /* measured time of one step with that configuration */
   int candidates;       /* configurations timed */
+  int prefetch_tiles;   /* L2 prefetch distance chosen (0 = off) */
 } lbm_tune_t;
 
 /* ---- lifecycle -------------------------------------------------------------- */
@@ -302,7 +305,8 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 /* ---- tuning ------------------------------------------------------------------- */
 
 /* Times the step kernel for each candidate form (variants 0 and 1 at blocks of 64
- * and 128 threads; the staged variants 2-4 where the domain allows them) on whole
+ * and 128 threads, each with L2 prefetch distances 0, 512, 1024 and 2048 tiles on
+ * whole-tile rows; the staged variants 2-4 where the domain allows them) on whole
  * step pairs with CUDA events on the handle's stream, and keeps the fastest in the
  * handle; returns it in *out if out != NULL. Needs an initialised state
  * (LBM_E_STATE otherwise); each candidate runs on the live state, so the state
@@ -318,6 +322,17 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
  * reports LBM_E_CUDA from the next synchronising call and refuses further steps
  * until a re-init. */
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
+
+/* Sets the L2 prefetch distance of the plain step kernel (variants 0 and 1) on
+ * domains of whole 32-cell tile rows (periodic x, nx a multiple of 32): the warp
+ * updating tile t first asks L2, with one bulk prefetch per slot run, for the slot
+ * blocks that the warp on tile t + tiles will read, so that warp's loads meet L2
+ * instead of DRAM (an implementation choice; the paper has no counterpart). 0 turns
+ * it off; held-x domains, other row lengths and the staged and batched forms ignore
+ * it. The default is 1024 tiles for 16-bit storage and 0 for FP32; lbm_autotune
+ * chooses among 0, 512, 1024 and 2048. Populations are bit-identical with any
+ * distance. LBM_E_INVAL for tiles < 0 or > 2^20 or a NULL handle. */
+lbm_status lbm_set_prefetch(lbm_handle* h, int tiles);
 
 /* Failure-detection test hook (no counterpart in the paper). With a staged kernel form
  * (variant 2-4), the next step does not issue the bulk copy of the first tile of one
@@ -383,12 +398,20 @@ lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int
                              int dtype);
 /* Total cells of all domains; time step of one domain. */
 lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain, double* dt);
-/* Times items per warp (1, 2, 4, 8 tiles of 32 cells) x block sizes x register
- * budgets of the persistent kernel and keeps the fastest; reports the cells per item,
- * the block size and the time per step (each pointer may be NULL). Advances the
- * state like lbm_autotune. */
+/* Times items per warp (1, 2, 4, 8, 16, 32 tiles of 32 cells) x block sizes x register
+ * budgets of the persistent kernel at the current L2 prefetch distance, then the
+ * distances 0, 512, 1024 and 2048 tiles for the fastest of those, and keeps the
+ * fastest; reports the cells per item, the block size, the time per step and the
+ * prefetch distance (each pointer may be NULL). Advances the state like lbm_autotune. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells,
-                              int* block_threads, float* ms_per_step);
+                              int* block_threads, float* ms_per_step, int* prefetch_tiles);
+/* L2 prefetch distance of the persistent kernel, in tiles (an implementation choice;
+ * the paper has no counterpart): a warp starting an item asks L2 for the slot blocks
+ * of the item that many tiles ahead in the claim order, in the pattern of
+ * lbm_set_prefetch. 0 turns it off; the default is 1024 for 16-bit storage and 0 for
+ * FP32. Populations are bit-identical with any distance. LBM_E_INVAL for tiles < 0 or
+ * > 2^20 or a NULL batch. */
+lbm_status lbm_batch_set_prefetch(lbm_batch* b, int tiles);
 
 #ifdef __cplusplus
 }

@@ -358,6 +358,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
     return fail(LBM_E_INVAL, "derived dt is not a positive finite number");
   }
   fill_const(p, h->dt, h->tau_R, h->tau_q, &h->P);
+  h->P.pf_tiles = p->store == LBM_STORE_F32 ? 0 : kDefaultPrefetch16;
   // Measured on GB300 at 512^3: blocks of 64 threads; the 170-register budget for
   // FP32 storage, the 128-register budget for 16-bit storage (lbm_autotune re-times).
   h->block_x = 64;
@@ -434,6 +435,7 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out) {
   out->store = h->prm.store;
   out->block_x = effective_block(h);
   out->variant = h->variant;
+  out->prefetch_tiles = h->P.pf_tiles;
   return LBM_OK;
 }
 
@@ -881,19 +883,24 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   if (h->nonfinite || h->stalled) return fail(LBM_E_STATE, "autotune on a failed state; re-init");
   if (pairs_per_trial < 1) pairs_per_trial = 4;
   struct Cand {
-    int variant, block;
+    int variant, block, prefetch;
   };
   std::vector<Cand> cands;
+  // The L2 prefetch applies to the plain forms on whole-tile rows only.
+  const bool rows = h->P.bc_x == 0 && h->P.nx % 32 == 0;
   for (int v : {0, 1})
     for (int b : {64, 128})
-      if (b <= 32 * ((h->P.nx + 31) / 32) || b == 64) cands.push_back({v, b});
+      if (b <= 32 * ((h->P.nx + 31) / 32) || b == 64)
+        for (int pf : {0, 512, 1024, 2048})
+          if (pf == 0 || rows) cands.push_back({v, b, pf});
   if (staged_eligible(h->P))
-    for (int v = kFirstStagedVariant; v <= kLastStagedVariant; ++v) cands.push_back({v, 128});
+    for (int v = kFirstStagedVariant; v <= kLastStagedVariant; ++v) cands.push_back({v, 128, 0});
   cudaEvent_t a, b;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
   int best_b = h->block_x, best_v = h->variant, best_grid = h->staged_grid, tried = 0;
+  int best_pf = h->P.pf_tiles;
   cudaError_t err = cudaSuccess;
   for (const Cand& c : cands) {
     int grid = 0;
@@ -906,6 +913,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
     h->block_x = c.block;
     h->variant = c.variant;
     h->staged_grid = grid;
+    h->P.pf_tiles = c.prefetch;
     for (int j = 0; j < 2 && err == cudaSuccess; ++j)  // warm-up pair
       err = step_launch(h, (int)((h->step + j) & 1), h->stream);
     h->step += 2;
@@ -925,6 +933,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
       best_b = c.block;
       best_v = c.variant;
       best_grid = grid;
+      best_pf = c.prefetch;
     }
   }
   cudaEventDestroy(a);
@@ -932,6 +941,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   h->block_x = best_b;
   h->variant = best_v;
   h->staged_grid = best_grid;
+  h->P.pf_tiles = best_pf;
   h->graphs_valid = false;
   if (err != cudaSuccess) return fail(LBM_E_CUDA, "autotune failed: %s", cudaGetErrorString(err));
   unsigned flag = 0;
@@ -944,6 +954,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
     out->variant = best_v;
     out->ms_per_step = best;
     out->candidates = tried;
+    out->prefetch_tiles = best_pf;
   }
   return LBM_OK;
 }
@@ -973,6 +984,15 @@ lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
     return fail(LBM_E_INVAL, "block_x must be 32, 64, 96 or 128");
   h->block_x = block_x;
   h->variant = variant;
+  h->graphs_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_prefetch(lbm_handle* h, int tiles) {
+  if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  if (tiles < 0 || tiles > kMaxPrefetch)
+    return fail(LBM_E_INVAL, "prefetch distance must be 0 to %d tiles", kMaxPrefetch);
+  h->P.pf_tiles = tiles;
   h->graphs_valid = false;
   return LBM_OK;
 }

@@ -26,12 +26,39 @@ using namespace lbm;
 namespace lbm {
 namespace batch_kernels {  // named: the host helpers below sit in an anonymous namespace
 
+// L2 prefetch for the tile a record names, in the pattern of the single-domain kernel:
+// even steps the tile's 7 slots, odd steps its slots 0-4 and, where a z plane holds
+// whole tiles (every size of the batched workloads), slot 6 of the tile a plane before
+// and slot 5 of the tile a plane after (periodic wrap). Only a hint.
+template <int PARITY, typename S>
+__device__ __forceinline__ void prefetch_tile_record(const DomainConst* sP, S* const* sPop, uint2 r) {
+  const int lo = (int)(r.x & 0xFFFFu);
+  const DomainConst& P = sP[lo];
+  const long long first = (long long)(r.x >> 16) +
+                          (long long)P.nx * ((long long)(r.y & 0xFFFFu) + (long long)P.ny * (r.y >> 16));
+  const long long w = first / kTile;  // a tile's first cell index is a multiple of 32
+  const S* pop = sPop[lo];
+  constexpr unsigned kSlotBytes = kSlotElems * sizeof(S);
+  if (PARITY == 0) {
+    l2_prefetch(pop + w * kTileElems, kQ * kSlotBytes);
+    return;
+  }
+  l2_prefetch(pop + w * kTileElems, 5 * kSlotBytes);
+  const long long plane = (long long)P.nx * P.ny;
+  if (plane % kTile) return;
+  const long long tpp = plane / kTile;
+  const long long zm = w >= tpp ? w - tpp : w - tpp + P.ntile;
+  const long long zp = w + tpp < P.ntile ? w + tpp : w + tpp - P.ntile;
+  l2_prefetch(pop + zm * kTileElems + 6 * kSlotElems, kSlotBytes);
+  l2_prefetch(pop + zp * kTileElems + 5 * kSlotElems, kSlotBytes);
+}
+
 template <int PARITY, int MINB, typename S, bool SR>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
                                                           const uint2* __restrict__ tiles,
                                                           int ndom, int total_tiles,
-                                                          int tiles_per_item,
+                                                          int tiles_per_item, int pf_items,
                                                           unsigned* __restrict__ next_item,
                                                           unsigned* __restrict__ flag) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -63,6 +90,11 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
   while (item < n_items) {
     if (lane == 0) claim = atomicAdd(next_item, 1u);
     const uint2 rec = records(item);
+    if (pf_items > 0) {  // the tiles of the item pf_items ahead, one per lane
+      const int fi = item + pf_items, ft = fi * tiles_per_item + lane;
+      if (fi < n_items && lane < tiles_per_item && ft < total_tiles)
+        prefetch_tile_record<PARITY, S>(sP, sPop, __ldg(&tiles[ft]));
+    }
     const int count = min(tiles_per_item, total_tiles - item * tiles_per_item);
     for (int j = 0; j < count; ++j) {
       // the tile's record: domain | x0 << 16, y0 | z0 << 16 (its first cell)
@@ -127,6 +159,7 @@ struct lbm_batch {
   unsigned* d_counter = nullptr;  // work-item counter of the persistent kernel
   int total_tiles = 0;
   int tiles_per_item = 4;      // layout tiles a warp takes at a time
+  int prefetch_tiles = 0;      // L2 prefetch distance in tiles (0: off)
   int block = 64;
   int variant = 0;             // register budget: 0 -> 3, 1 -> 4 blocks of 128 per SM
   int grid = 0;
@@ -213,10 +246,12 @@ lbm_status size_grid(lbm_batch* b) {
 template <typename S, bool SR>
 void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
   const dim3 g(b->grid), bl(b->block);
+  const int pf_items = b->prefetch_tiles > 0 ? std::max(1, b->prefetch_tiles / b->tiles_per_item) : 0;
 #define LBM_BATCH_LAUNCH(PAR, MB)                                                           \
   k_batch_step<PAR, MB, S, SR><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, \
                                                       b->n, b->total_tiles,                 \
-                                                      b->tiles_per_item, b->d_counter, b->flag)
+                                                      b->tiles_per_item, pf_items, b->d_counter, \
+                                                      b->flag)
   if (b->variant) {
     if (parity) LBM_BATCH_LAUNCH(1, 4);
     else LBM_BATCH_LAUNCH(0, 4);
@@ -279,6 +314,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   b->n = n;
   b->store = params[0].store;
   b->sround = params[0].stochastic_round != 0 && params[0].store != LBM_STORE_F32;
+  b->prefetch_tiles = b->store == LBM_STORE_F32 ? 0 : kDefaultPrefetch16;
   size_t bytes = 0;
   for (int d = 0; d < n; ++d) {
     lbm_status s = validate(&params[d]);
@@ -303,6 +339,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     derive(&params[d], &dt, &tR, &tq);
     DomainConst P;
     fill_const(&params[d], dt, tR, tq, &P);
+    P.pf_tiles = b->store == LBM_STORE_F32 ? 0 : kDefaultPrefetch16;  // the sequential launches
     b->P.push_back(P);
     b->dt.push_back(dt);
     b->tau_R.push_back(tR);
@@ -524,7 +561,7 @@ lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain
 }
 
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells, int* block_threads,
-                              float* ms_per_step) {
+                              float* ms_per_step, int* prefetch_tiles) {
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
   if (!b->initialized) return fail(LBM_E_STATE, "autotune needs an initialised batch");
   if (steps_per_trial < 2) steps_per_trial = 8;
@@ -535,44 +572,77 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells
   cudaEvent_t a, e;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&e));
+  // Mean time of one step of the current configuration over steps_per_trial steps
+  // (after a warm-up pair).
+  auto trial = [&](float* ms) -> lbm_status {
+    lbm_status s = size_grid(b);
+    if (s != LBM_OK) return s;
+    for (int j = 0; j < 2; ++j) LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
+    b->step += 2;
+    LBM_CUDA(cudaEventRecord(a, b->stream));
+    for (int j = 0; j < steps_per_trial; ++j)
+      LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
+    b->step += steps_per_trial;
+    LBM_CUDA(cudaEventRecord(e, b->stream));
+    LBM_CUDA(cudaEventSynchronize(e));
+    LBM_CUDA(cudaEventElapsedTime(ms, a, e));
+    *ms /= (float)steps_per_trial;
+    return LBM_OK;
+  };
   float best = 1e30f;
   int best_i = b->tiles_per_item, best_b = b->block, best_v = b->variant;
+  lbm_status st = LBM_OK;
+  // First items x blocks x budgets at the current prefetch distance, then the
+  // distance for the fastest of them.
   for (int v : variants)
     for (int bl : blocks)
       for (int it : items) {
+        if (st != LBM_OK) break;
         b->variant = v;
         b->block = bl;
         b->tiles_per_item = it;
-        lbm_status s = size_grid(b);
-        if (s != LBM_OK) return s;
-        for (int j = 0; j < 2; ++j) LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
-        b->step += 2;
-        LBM_CUDA(cudaEventRecord(a, b->stream));
-        for (int j = 0; j < steps_per_trial; ++j)
-          LBM_CUDA(launch_batch(b, (int)((b->step + j) & 1), b->stream));
-        b->step += steps_per_trial;
-        LBM_CUDA(cudaEventRecord(e, b->stream));
-        LBM_CUDA(cudaEventSynchronize(e));
         float ms = 0;
-        LBM_CUDA(cudaEventElapsedTime(&ms, a, e));
-        ms /= (float)steps_per_trial;
-        if (ms < best) {
+        st = trial(&ms);
+        if (st == LBM_OK && ms < best) {
           best = ms;
           best_i = it;
           best_b = bl;
           best_v = v;
         }
       }
-  cudaEventDestroy(a);
-  cudaEventDestroy(e);
   b->tiles_per_item = best_i;
   b->block = best_b;
   b->variant = best_v;
+  int best_pf = b->prefetch_tiles;
+  for (int pf : {0, 512, 1024, 2048}) {
+    if (st != LBM_OK || pf == best_pf) continue;
+    b->prefetch_tiles = pf;
+    float ms = 0;
+    st = trial(&ms);
+    if (st == LBM_OK && ms < best) {
+      best = ms;
+      best_pf = pf;
+    }
+  }
+  b->prefetch_tiles = best_pf;
+  cudaEventDestroy(a);
+  cudaEventDestroy(e);
+  if (st != LBM_OK) return st;
   lbm_status s = size_grid(b);
   if (s != LBM_OK) return s;
   if (tile_cells) *tile_cells = best_i * kTile;
   if (block_threads) *block_threads = best_b;
   if (ms_per_step) *ms_per_step = best;
+  if (prefetch_tiles) *prefetch_tiles = best_pf;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_prefetch(lbm_batch* b, int tiles) {
+  if (!b) return fail(LBM_E_INVAL, "batch is NULL");
+  if (tiles < 0 || tiles > kMaxPrefetch)
+    return fail(LBM_E_INVAL, "prefetch distance must be 0 to %d tiles", kMaxPrefetch);
+  b->prefetch_tiles = tiles;
+  b->graphs_valid = false;
   return LBM_OK;
 }
 

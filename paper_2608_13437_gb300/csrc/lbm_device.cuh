@@ -48,6 +48,7 @@ struct DomainConst {
   float scale[kF], inv_scale[kF];
   int sutherland, sensor_mode, collide;
   int sround;         // 16-bit storage rounds stochastically (1) or to nearest (0)
+  int pf_tiles;       // L2 prefetch distance of the plain step kernel on whole-tile rows (0: off)
   double dx64;        // dx in FP64 (the diagnostics' gradient pass takes 1/dx from it)
 };
 

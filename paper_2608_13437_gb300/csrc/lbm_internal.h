@@ -35,6 +35,12 @@ cudaError_t launch_step_bf16(const DomainConst& P, int parity, void* pop, const 
 // is a failure-detection test hook (one warp's first copy is not issued, so its
 // bounded wait runs out and the step reports a stalled copy).
 constexpr int kFirstStagedVariant = 2, kLastStagedVariant = 4;
+// L2 prefetch distance (tiles ahead) of the plain and batched step kernels for 16-bit
+// storage when not tuned: about half the warps resident on the GPU at once, the
+// fastest distance measured at 512^3 (FP32 storage gains nothing from it and starts
+// with 0); the largest distance accepted.
+constexpr int kDefaultPrefetch16 = 1024;
+constexpr int kMaxPrefetch = 1 << 20;
 inline bool staged_eligible(const DomainConst& P) {
   return P.bc_x == 0 && P.nx % 32 == 0 && P.sround == 0;  // no stochastic rounding there
 }

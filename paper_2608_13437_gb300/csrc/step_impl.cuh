@@ -50,6 +50,37 @@ __device__ __forceinline__ void link_tile(const WarpTiles& T, int i, int toward,
   }
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Whole-tile rows: tiles are processed roughly in index order, so the warp on tile t
+// asks L2 for the slot blocks that the warp on tile w = t + P.pf_tiles will read, and
+// that warp later finds them in L2 instead of waiting on DRAM. Even steps read the 7
+// slots of the own tile. Odd steps read slots 0-2 of the own tile, slot 4 of the tile
+// a row before, slot 3 of the tile a row after, slot 6 of the tile a plane before and
+// slot 5 of the tile a plane after; prefetching slots 0-4 of tile w (its slots 3 and 4
+// serve the warps a row before and after w) and the two plane slots covers them.
+// Only addresses inside the buffer are prefetched (periodic wrap along z); results
+// do not depend on the prefetch.
+template <int PARITY, typename S>
+__device__ __forceinline__ void prefetch_future(const DomainConst& P, const S* pop, long long t) {
+  const long long w = t + P.pf_tiles;
+  if (w >= P.ntile) return;
+  constexpr unsigned kSlotBytes = kSlotElems * sizeof(S);
+  if (PARITY == 0) {
+    l2_prefetch(pop + w * kTileElems, kQ * kSlotBytes);
+  } else {
+    const long long tpp = (long long)(P.nx / kTile) * P.ny;
+    const long long zm = w >= tpp ? w - tpp : w - tpp + P.ntile;
+    const long long zp = w + tpp < P.ntile ? w + tpp : w + tpp - P.ntile;
+    l2_prefetch(pop + w * kTileElems, 5 * kSlotBytes);
+    l2_prefetch(pop + zm * kTileElems + 6 * kSlotElems, kSlotBytes);
+    l2_prefetch(pop + zp * kTileElems + 5 * kSlotElems, kSlotBytes);
+  }
+}
+
 // load_cell for whole-tile rows: even steps read slot i of the own cell, odd steps
 // slot opp(i) of cell x - e_i.
 template <int PARITY, typename S>
@@ -108,6 +139,7 @@ __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __re
     if (x0 >= P.nx) return;  // whole warps (nx is a multiple of 32)
     const int lane = threadIdx.x & (kTile - 1);
     const WarpTiles T = warp_tiles(P, x0, blockIdx.y, blockIdx.z);
+    if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S>(P, pop, T.t);
     load_cell_rows<PARITY, S>(P, pop, T, lane, d);
     if (P.collide) {
       const float probe = collide_cell<false>(P, d, nullptr);

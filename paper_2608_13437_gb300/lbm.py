@@ -43,7 +43,7 @@ class LbmInfo(ctypes.Structure):
         ("tau_q", ctypes.c_double), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
         ("scale", ctypes.c_double * 14), ("step", ctypes.c_longlong), ("ncell", ctypes.c_longlong),
         ("population_bytes", ctypes.c_size_t), ("store", ctypes.c_int), ("block_x", ctypes.c_int),
-        ("variant", ctypes.c_int),
+        ("variant", ctypes.c_int), ("prefetch_tiles", ctypes.c_int),
     ]
 
 
@@ -57,7 +57,7 @@ class LbmDiag(ctypes.Structure):
 
 class LbmTune(ctypes.Structure):
     _fields_ = [("block_x", ctypes.c_int), ("variant", ctypes.c_int), ("ms_per_step", ctypes.c_float),
-                ("candidates", ctypes.c_int)]
+                ("candidates", ctypes.c_int), ("prefetch_tiles", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -101,6 +101,7 @@ _SIGNATURES = {
     "lbm_load": (_IP, [_VP, ctypes.c_char_p]),
     "lbm_autotune": (_IP, [_VP, _IP, ctypes.POINTER(LbmTune)]),
     "lbm_set_kernel_config": (_IP, [_VP, _IP, _IP]),
+    "lbm_set_prefetch": (_IP, [_VP, _IP]),
     "lbm_batch_create": (_IP, [_IP, ctypes.POINTER(LbmParams), ctypes.POINTER(_VP)]),
     "lbm_batch_destroy": (_IP, [_VP]),
     "lbm_batch_init_tgv": (_IP, [_VP, _DP, _DP, _DP]),
@@ -110,7 +111,8 @@ _SIGNATURES = {
     "lbm_batch_moments": (_IP, [_VP, _IP, _IP, _VP, _IP, _IP]),
     "lbm_batch_info": (_IP, [_VP, ctypes.POINTER(ctypes.c_longlong), _IP, _DP]),
     "lbm_batch_autotune": (_IP, [_VP, _IP, ctypes.POINTER(_IP), ctypes.POINTER(_IP),
-                                 ctypes.POINTER(ctypes.c_float)]),
+                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_IP)]),
+    "lbm_batch_set_prefetch": (_IP, [_VP, _IP]),
 }
 
 
@@ -351,11 +353,14 @@ class Domain:
     def set_kernel_config(self, block_x: int, variant: int):
         check(lib().lbm_set_kernel_config(self._h, int(block_x), int(variant)))
 
+    def set_prefetch(self, tiles: int):
+        check(lib().lbm_set_prefetch(self._h, int(tiles)))
+
     def autotune(self, pairs_per_trial=4) -> dict:
         t = LbmTune()
         check(lib().lbm_autotune(self._h, int(pairs_per_trial), ctypes.byref(t)))
         return {"block_x": t.block_x, "variant": t.variant, "ms_per_step": t.ms_per_step,
-                "candidates": t.candidates}
+                "candidates": t.candidates, "prefetch_tiles": t.prefetch_tiles}
 
 
 class Batch:
@@ -418,11 +423,15 @@ class Batch:
         check(lib().lbm_batch_info(self._h, None, int(d), ctypes.byref(v)))
         return float(v.value)
 
+    def set_prefetch(self, tiles: int):
+        check(lib().lbm_batch_set_prefetch(self._h, int(tiles)))
+
     def autotune(self, steps_per_trial=4) -> dict:
-        tc, bt, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        tc, bt, ms, pf = ctypes.c_int(), ctypes.c_int(), ctypes.c_float(), ctypes.c_int()
         check(lib().lbm_batch_autotune(self._h, int(steps_per_trial), ctypes.byref(tc),
-                                       ctypes.byref(bt), ctypes.byref(ms)))
-        return {"tile_cells": tc.value, "block": bt.value, "ms_per_step": ms.value}
+                                       ctypes.byref(bt), ctypes.byref(ms), ctypes.byref(pf)))
+        return {"tile_cells": tc.value, "block": bt.value, "ms_per_step": ms.value,
+                "prefetch_tiles": pf.value}
 
 
 def encode_pairs(store, values, rbits=None):

@@ -91,12 +91,12 @@ def test_every_entry_point_rejects_a_null_handle(L):
         "lbm_step_diag": (V, 1, V), "lbm_diag_static": (V, V),
         "lbm_populations_get": (V, buf, 0, 0), "lbm_populations_set": (V, buf, 0, 0),
         "lbm_save": (V, b"x"), "lbm_load": (V, b"x"), "lbm_autotune": (V, 1, V),
-        "lbm_set_kernel_config": (V, 64, 0), "lbm_test_skip_copy": (V,),
+        "lbm_set_kernel_config": (V, 64, 0), "lbm_set_prefetch": (V, 0), "lbm_test_skip_copy": (V,),
         "lbm_plane_get": (V, 0, 0, buf, 0), "lbm_plane_set": (V, 0, 0, buf, 0),
         "lbm_batch_init_tgv": (V, d3, d3, d3), "lbm_batch_step": (V, 1),
         "lbm_batch_step_sequential": (V, 1), "lbm_batch_synchronize": (V,),
         "lbm_batch_moments": (V, 0, 0, buf, 0, 0), "lbm_batch_info": (V, V, 0, V),
-        "lbm_batch_autotune": (V, 1, V, V, V),
+        "lbm_batch_autotune": (V, 1, V, V, V, V), "lbm_batch_set_prefetch": (V, 0),
         "lbm_test_encode": (1, 0, V, V, V, 4, V),
     }
     for name, args in calls.items():

@@ -129,3 +129,33 @@ def test_reduced_storage_batch_matches_single_domains(lbm, store, sr):
         one.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+def test_batch_prefetch_distances_agree_bitwise(lbm, store):
+    """The persistent kernel's L2 prefetch is only a hint: off, distances that land
+    inside these small domains (and across domain boundaries), and the 16-bit default
+    give the same moments bit for bit after an odd number of steps, with items of one
+    and of four tiles."""
+    params, ic = _small_batch()
+    ref = None
+    for pf in (0, 1, 5, 64, 1024):
+        B = lbm.Batch(params, store=store)
+        B.set_prefetch(pf)
+        B.init_tgv([c["U0"] for c in ic], [c["M0"] for c in ic], [c["rho0"] for c in ic])
+        B.step(21)
+        B.synchronize()
+        q = [B.moments(d) for d in range(len(params))]
+        B.close()
+        if ref is None:
+            ref = q
+        else:
+            for d in range(len(params)):
+                assert np.array_equal(q[d], ref[d]), (pf, d)
+    with pytest.raises(lbm.LbmError) as ei:
+        B = lbm.Batch(params, store=store)
+        try:
+            B.set_prefetch(-1)
+        finally:
+            B.close()
+    assert ei.value.status == lbm.LBM_E_INVAL

@@ -388,7 +388,9 @@ def test_staged_variants_need_whole_tile_rows(lbm):
     e = lbm.Domain(q, store="f16")
     e.init_tgv(1.0, 1.25, 1.0)
     t = e.autotune(pairs_per_trial=1)
-    assert t["candidates"] == 7
+    assert t["candidates"] == 19  # 2 budgets x 2 blocks x 4 prefetch distances + 3 staged
+    assert t["prefetch_tiles"] in (0, 512, 1024, 2048)
+    assert e.info()["prefetch_tiles"] == t["prefetch_tiles"]
     e.close()
 
 
@@ -539,6 +541,49 @@ def test_stochastic_rounding_is_reproducible_across_kernel_forms(lbm, store):
                 d.set_kernel_config(64, 2)
             assert ei.value.status == lbm.LBM_E_INVAL
             d.close()
+
+
+@pytest.mark.parametrize("store,sr", [("f32", 0), ("f16", 0), ("bf16", 0), ("f16", 1)])
+def test_prefetch_distances_agree_bitwise(lbm, store, sr):
+    """The L2 prefetch of the plain step kernel is only a hint: every distance (off,
+    short ones that land inside these small domains, with the periodic z wrap, and the
+    16-bit default) gives the same populations bit for bit over both parities, on rows
+    of one to three tiles and y, z extents from 1 to 5."""
+    for nx, ny, nz in ((64, 5, 3), (32, 1, 4), (96, 3, 1)):
+        p = inputs.tgv_params(16)
+        p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / nx, sutherland=0, f_mu=0.3, J_min=1e-3,
+                 tau_R=0.05, tau_q=0.05, stochastic_round=sr)
+        s = inputs.random_smooth_state(nx, ny, nz, seed=47, amp=0.15)
+        ref = None
+        for pf in (0, 1, 3, 7, 1024):
+            d = lbm.Domain(p, store=store)
+            d.set_kernel_config(64, 0)
+            d.set_prefetch(pf)
+            assert d.info()["prefetch_tiles"] == pf
+            d.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"])
+            d.step(23)
+            d.synchronize()
+            f = d.populations("native")
+            d.close()
+            if ref is None:
+                ref = f
+            else:
+                assert np.array_equal(f, ref), (nx, ny, nz, pf)
+
+
+def test_prefetch_defaults_and_limits(lbm):
+    """16-bit storage starts with a prefetch distance of 1024 tiles, FP32 with none;
+    distances outside 0..2^20 are refused."""
+    p = inputs.tgv_params(16)
+    for store, default in (("f32", 0), ("f16", 1024), ("bf16", 1024)):
+        d = lbm.Domain(p, store=store)
+        assert d.info()["prefetch_tiles"] == default
+        for bad in (-1, (1 << 20) + 1):
+            with pytest.raises(lbm.LbmError) as ei:
+                d.set_prefetch(bad)
+            assert ei.value.status == lbm.LBM_E_INVAL
+        d.set_prefetch(1 << 20)
+        d.close()
 
 
 def test_graphs_and_direct_launches_agree_bitwise(lbm):
