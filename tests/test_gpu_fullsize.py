@@ -7,6 +7,8 @@
     periodic corner;
   * 512^3: the TMA-staged step form against the plain kernel (bit for bit, on the
     device) and the in-step diagnostics against the separate pass;
+  * 512^3: the plain step with and without its L2 prefetch (bit for bit, FP32 and
+    FP16);
   * dissipation time series per storage type against the oracle (64^3, 400 steps);
   * Sod at 256..2048 cells: shock position, first-order thickness, L1 falling;
   * reduced storage at 128^3 against the FP64 oracle and the FP32 GPU path;
@@ -134,6 +136,30 @@ def test_512_staged_form_and_in_step_diagnostics(lbm):
     for k in ("sum_rho", "sum_E", "ek_mean"):
         assert got[k] == pytest.approx(ref[k], rel=1e-11), k
     a.close()
+
+
+@pytest.mark.parametrize("store,pf", [("f32", 512), ("f16", 1024)])
+def test_512_prefetch_form_is_bitwise_equal(lbm, store, pf):
+    """At 512^3 the plain step with its L2 prefetch (the distance the autotuner picks
+    for this size) equals the step without it bit for bit after an odd number of
+    steps, compared on the device."""
+    import torch
+    p = inputs.tgv_params(512)
+    a = lbm.Domain(p, store=store)
+    b = lbm.Domain(p, store=store)
+    a.set_kernel_config(64, 0)
+    b.set_kernel_config(64, 0)
+    a.set_prefetch(0)
+    b.set_prefetch(pf)
+    for d in (a, b):
+        d.init_tgv(1.0, 1.25, 1.0)
+        d.step(3)
+        d.synchronize()
+    assert torch.equal(a._buf, b._buf)
+    a.close()
+    b.close()
+    del a, b
+    torch.cuda.empty_cache()
 
 
 def test_dissipation_curves_per_storage_type(lbm, oracle_mod):
