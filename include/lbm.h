@@ -55,7 +55,9 @@ typedef enum {
   LBM_E_CUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
   LBM_E_NONFINITE = 4,  /* a non-finite moment was detected; sticky until re-init */
   LBM_E_STATE = 5,      /* call not valid in the current state (e.g. step before init) */
-  LBM_E_IO = 6          /* checkpoint file could not be read or written, or is corrupt */
+  LBM_E_IO = 6,         /* checkpoint file could not be read or written, or is corrupt */
+  LBM_E_TIMEOUT = 7     /* a bounded wait inside a kernel ran out (a staged step's wait for its
+                           own bulk copy): the state is incomplete; sticky until re-init */
 } lbm_status;
 
 /* Population storage. All arithmetic is FP32 in every mode.
@@ -319,7 +321,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
  * periodic x axis, nx a multiple of 32 (whole 32-cell tiles per row) and rounding to
  * nearest (LBM_E_INVAL otherwise). All forms compute bit-identical populations. A staged step whose wait
  * for a copy runs out (bounded; it does not happen in normal operation) stops,
- * reports LBM_E_CUDA from the next synchronising call and refuses further steps
+ * reports LBM_E_TIMEOUT from the next synchronising call and refuses further steps
  * until a re-init. */
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant);
 
@@ -338,7 +340,7 @@ lbm_status lbm_set_prefetch(lbm_handle* h, int tiles);
  * (variant 2-4), the next step does not issue the bulk copy of the first tile of one
  * warp (block 0, warp 0), so that warp's bounded wait for it runs out after about a
  * second; nothing faults or hangs. The step then ends early and the next
- * synchronising call (lbm_synchronize, lbm_diag) returns LBM_E_CUDA, after which
+ * synchronising call (lbm_synchronize, lbm_diag) returns LBM_E_TIMEOUT, after which
  * lbm_step refuses to run until a re-init. LBM_E_INVAL for a plain form. */
 lbm_status lbm_test_skip_copy(lbm_handle* h);
 

@@ -340,6 +340,7 @@ const char* lbm_status_string(lbm_status s) {
     case LBM_E_NONFINITE: return "LBM_E_NONFINITE";
     case LBM_E_STATE: return "LBM_E_STATE";
     case LBM_E_IO: return "LBM_E_IO";
+    case LBM_E_TIMEOUT: return "LBM_E_TIMEOUT";
   }
   return "unknown status";
 }
@@ -556,7 +557,7 @@ lbm_status lbm_step(lbm_handle* h, int n) {
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
-  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (h->stalled) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   if (n == 0) return LBM_OK;
   if (!h->prm.use_graphs) {
     for (int j = 0; j < n; ++j) {
@@ -596,7 +597,7 @@ lbm_status lbm_synchronize(lbm_handle* h) {
   LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   latch_flag(h, flag);
-  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (h->stalled) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
 }
@@ -727,7 +728,7 @@ static lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, lon
   out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
   latch_flag(h, flag);
   if (r[6] > 0) h->nonfinite = true;
-  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (h->stalled) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
 }
@@ -753,7 +754,7 @@ lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
   if (n < 1) return fail(LBM_E_INVAL, "n must be >= 1");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step_diag before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
-  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (h->stalled) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   lbm_status st = ensure_diag_scratch(h);
   if (st != LBM_OK) return st;
   const int bx = effective_block(h);
@@ -948,7 +949,7 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   latch_flag(h, flag);
-  if (h->stalled) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (h->stalled) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   if (out) {
     out->block_x = best_v >= kFirstStagedVariant ? 128 : effective_block(h);
     out->variant = best_v;

@@ -109,7 +109,7 @@ extern "C" lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out) {
   out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
   latch_step_flag(h, flag);
   if (r[6] > 0) latch_nonfinite(h);
-  if (stall_latched(h)) return fail(LBM_E_CUDA, "a staged step gave up waiting for a bulk copy; re-init");
+  if (stall_latched(h)) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
   if (nonfinite_latched(h)) return fail(LBM_E_NONFINITE, "non-finite moments detected");
   return LBM_OK;
 }

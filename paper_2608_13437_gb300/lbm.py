@@ -15,7 +15,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
 
-LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NONFINITE, LBM_E_STATE, LBM_E_IO = range(7)
+LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NONFINITE, LBM_E_STATE, LBM_E_IO, LBM_E_TIMEOUT = range(8)
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 DT_F32, DT_F64, DT_NATIVE = 0, 1, 2
 MOM_Q, MOM_PRIM = 0, 1
@@ -67,7 +67,7 @@ class LbmError(RuntimeError):
 
 
 _STATUS_NAMES = {0: "LBM_OK", 1: "LBM_E_INVAL", 2: "LBM_E_NOMEM", 3: "LBM_E_CUDA",
-                 4: "LBM_E_NONFINITE", 5: "LBM_E_STATE", 6: "LBM_E_IO"}
+                 4: "LBM_E_NONFINITE", 5: "LBM_E_STATE", 6: "LBM_E_IO", 7: "LBM_E_TIMEOUT"}
 
 _lib = None
 

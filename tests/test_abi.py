@@ -73,6 +73,7 @@ def test_null_arguments_are_rejected(L):
     assert L.lbm_step_diag(None, 1, ctypes.byref(lbm.LbmDiag())) == lbm.LBM_E_INVAL
     assert L.lbm_destroy(None) == lbm.LBM_OK
     assert L.lbm_status_string(4) == b"LBM_E_NONFINITE"
+    assert L.lbm_status_string(7) == b"LBM_E_TIMEOUT"
     assert L.lbm_batch_create(0, None, ctypes.byref(ctypes.c_void_p())) == lbm.LBM_E_INVAL
 
 

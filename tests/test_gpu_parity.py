@@ -397,7 +397,7 @@ def test_staged_variants_need_whole_tile_rows(lbm):
 def test_staged_copy_wait_runs_out_and_is_reported(lbm):
     """Failure detection without a fault: the test hook keeps one warp's first bulk copy
     from being issued, so its bounded wait (about a second) runs out. The step ends, the
-    next synchronising call reports LBM_E_CUDA, further steps are refused, and after a
+    next synchronising call reports LBM_E_TIMEOUT, further steps are refused, and after a
     re-init the same handle steps exactly like a fresh one (the context stayed usable)."""
     import time
     p = inputs.tgv_params(32)
@@ -410,11 +410,11 @@ def test_staged_copy_wait_runs_out_and_is_reported(lbm):
     d.step(3)
     with pytest.raises(lbm.LbmError) as ei:
         d.synchronize()
-    assert ei.value.status == lbm.LBM_E_CUDA and "bulk copy" in str(ei.value)
+    assert ei.value.status == lbm.LBM_E_TIMEOUT and "bulk copy" in str(ei.value)
     assert time.time() - t0 < 30
     with pytest.raises(lbm.LbmError) as ei:
         d.step(1)
-    assert ei.value.status == lbm.LBM_E_CUDA
+    assert ei.value.status == lbm.LBM_E_TIMEOUT
     d.init_tgv(1.0, 1.25, 1.0)
     d.step(7)
     d.synchronize()
