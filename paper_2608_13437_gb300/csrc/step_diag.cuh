@@ -7,12 +7,15 @@
 
 #include "diag_device.cuh"
 #include "lbm_internal.h"
+#include "step_impl.cuh"
 
 namespace lbm {
 
 static_assert(kDiagRecFloats == kDiagRecWords, "warp record size");
 
-template <int PARITY, typename S, bool HELD, bool SR>
+// ROWS: whole-tile rows (periodic x, nx a multiple of 32) take the plain kernel's
+// warp-uniform tile addressing and its L2 prefetch; every warp is then whole.
+template <int PARITY, typename S, bool HELD, bool SR, bool ROWS>
 __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __restrict__ pop,
                                                       const float* __restrict__ ghost,
                                                       unsigned* __restrict__ flag,
@@ -21,19 +24,35 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   DiagAcc acc;
   diag_zero(acc);
-  if (x < P.nx) {  // no early return: every lane takes part in the warp reduction
-    const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
+  const int lane = threadIdx.x & (kTile - 1);
+  // no early return: every lane takes part in the warp reduction
+  if (ROWS ? (x - lane < P.nx) : (x < P.nx)) {
     float d[kF][kQ];
-    load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
     CellDiag cd;
-    if (P.collide) {
-      const float probe = collide_cell<false, true>(P, d, nullptr, &cd);
-      if (!isfinite(probe)) atomicOr(flag, 1u);
+    if constexpr (ROWS) {
+      const WarpTiles T = warp_tiles(P, x - lane, blockIdx.y, blockIdx.z);
+      if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S>(P, pop, T.t);
+      load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+      if (P.collide) {
+        const float probe = collide_cell<false, true>(P, d, nullptr, &cd);
+        if (!isfinite(probe)) atomicOr(flag, 1u);
+      } else {
+        SensorOut so;
+        collide_cell<true, true>(P, d, &so, &cd);
+      }
+      store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
     } else {
-      SensorOut so;
-      collide_cell<true, true>(P, d, &so, &cd);
+      const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
+      load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
+      if (P.collide) {
+        const float probe = collide_cell<false, true>(P, d, nullptr, &cd);
+        if (!isfinite(probe)) atomicOr(flag, 1u);
+      } else {
+        SensorOut so;
+        collide_cell<true, true>(P, d, &so, &cd);
+      }
+      store_cell<PARITY, S, SR>(P, pop, c, d);
     }
-    store_cell<PARITY, S, SR>(P, pop, c, d);
     diag_add_cell(P, cd, acc);
     const long long n = P.ncell;
     const long long cell = x + (long long)P.nx * (blockIdx.y + (long long)P.ny * blockIdx.z);
@@ -43,7 +62,7 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
     ufield[3 * n + cell] = cd.mu_T;
   }
   diag_warp_reduce(acc);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     diag_store_words(acc, rec + (blk * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDiagRecWords);
   }
@@ -54,11 +73,14 @@ void launch_step_diag_forms(const DomainConst& P, int parity, S* p, const float*
                             unsigned* flag, float* ufield, float* rec, dim3 grid, dim3 block,
                             cudaStream_t s) {
   if (P.bc_x) {
-    if (parity) k_step_diag<1, S, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
-    else k_step_diag<0, S, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    if (parity) k_step_diag<1, S, true, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, true, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  } else if (P.nx % kTile == 0) {
+    if (parity) k_step_diag<1, S, false, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, false, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
   } else {
-    if (parity) k_step_diag<1, S, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
-    else k_step_diag<0, S, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    if (parity) k_step_diag<1, S, false, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, false, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
   }
 }
 
