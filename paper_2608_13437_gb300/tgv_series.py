@@ -3,7 +3,8 @@ the solenoidal and dilatational dissipation rates (Eq. 7), computed inside the s
 every `every` steps (lbm_step_diag; FP64 global sums).
 
     python -m paper_2608_13437_gb300.tgv_series --n 256 --steps 20000 --every 100 \
-        [--store f32] [--M0 1.25] [--Re 1000] [--spectral-every K] [--t-end T] [--out series.json]
+        [--store f32] [--M0 1.25] [--Re 1000] [--spectral-every K] [--t-end T]
+        [--param NAME=VALUE ...] [--out series.json]
 
 Prints one JSON object: the workload, and per sample the step, convective time
 t_c = t U0 / L, E_k / (rho0 U0^2), eps_s and eps_d divided by rho_ref = rho0, the
@@ -20,7 +21,8 @@ import time
 
 
 def run(n: int, steps: int, every: int, store: str = "f32", M0: float = 1.25, Re: float = 1000.0,
-        U0: float = 1.0, rho0: float = 1.0, spectral_every: int = 0, t_end: float = 0.0) -> dict:
+        U0: float = 1.0, rho0: float = 1.0, spectral_every: int = 0, t_end: float = 0.0,
+        overrides: dict | None = None) -> dict:
     import math
 
     import torch
@@ -28,6 +30,7 @@ def run(n: int, steps: int, every: int, store: str = "f32", M0: float = 1.25, Re
     from paper_2608_13437_gb300 import inputs, lbm, spectral
     torch.cuda.set_device(0)
     p = inputs.tgv_params(n, M0=M0, Re=Re, U0=U0, rho0=rho0)
+    p.update(overrides or {})
     dom = lbm.Domain(p, store=store)
     dom.init_tgv(U0, M0, rho0)
     if t_end > 0:
@@ -64,7 +67,8 @@ def run(n: int, steps: int, every: int, store: str = "f32", M0: float = 1.25, Re
     wall = time.perf_counter() - t0
     info = dom.info()
     dom.close()
-    out = {"workload": f"supersonic TGV {n}^3, M0 {M0}, Re {Re}, store {store}",
+    out = {"workload": f"supersonic TGV {n}^3, M0 {M0}, Re {Re}, store {store}"
+                       + "".join(f", {k} {v}" for k, v in (overrides or {}).items()),
            "dt": info["dt"], "steps": steps, "wall_s": round(wall, 2),
            "mlups_including_diagnostics": round(n ** 3 * steps / wall / 1e6, 1),
            "samples": samples}
@@ -105,10 +109,16 @@ def main():
     ap.add_argument("--Re", type=float, default=1000.0)
     ap.add_argument("--spectral-every", type=int, default=0)
     ap.add_argument("--t-end", type=float, default=0.0)
+    ap.add_argument("--param", action="append", default=[], metavar="NAME=VALUE",
+                    help="override one domain parameter (e.g. sensor_mode=1, C_sigma=20)")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
+    overrides = {}
+    for item in a.param:
+        name, value = item.split("=", 1)
+        overrides[name] = int(value) if value.lstrip("-").isdigit() else float(value)
     res = run(a.n, a.steps, a.every, a.store, a.M0, a.Re, spectral_every=a.spectral_every,
-              t_end=a.t_end)
+              t_end=a.t_end, overrides=overrides)
     text = json.dumps(res)
     if a.out:
         with open(a.out, "w") as fh:
