@@ -156,3 +156,38 @@ def test_batch_rejects_more_domains_or_wider_rows_than_its_tile_records_hold(L):
     assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
     assert not b.value
     assert b"nx <= 65535" in L.lbm_last_error()
+
+
+def test_header_compiles_as_c_and_binding_layouts_match(tmp_path):
+    """include/lbm.h is plain C (gcc -std=c99) and C++, and the ctypes structures of the
+    binding have the sizes and field offsets of the header's structs."""
+    import shutil
+    import subprocess
+
+    from paper_2608_13437_gb300 import lbm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"lbm_params": lbm.LbmParams, "lbm_info_t": lbm.LbmInfo,
+               "lbm_tune_t": lbm.LbmTune, "lbm_diag_t": lbm.LbmDiag}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)], check=True)
+    cxx = shutil.which("g++")
+    if cxx:
+        subprocess.run([cxx, "-x", "c++", "-fsyntax-only", "-Wall", "-Werror", "-I", inc, str(src)],
+                       check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
