@@ -386,7 +386,9 @@ lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int sr
  * replayed from a CUDA graph; lbm_batch_step_sequential issues one plain launch per
  * domain per step instead. Both give bit-identical populations. Items per warp,
  * block size and register budget come from lbm_batch_autotune. At most a few
- * hundred domains per batch (their constants must fit in shared memory). */
+ * hundred domains per batch (their constants must fit in shared memory), and each
+ * domain's nx at most 65535 (the per-tile records hold 16-bit domain indices and
+ * coordinates); LBM_E_INVAL otherwise, before any CUDA call. */
 lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out);
 lbm_status lbm_batch_destroy(lbm_batch* b);
 /* Per-domain TGV parameters, arrays of n values (host). */
