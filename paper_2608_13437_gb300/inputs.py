@@ -228,3 +228,22 @@ def tgv_fields(n: int, M0: float = 1.25, U0: float = 1.0, rho0: float = 1.0,
         out[4, z] = p
         out[0, z] = p / T0
     return out
+
+
+def separable_wave_fields(nx: int, ny: int, nz: int, A: float, k: int, rho0: float, T0: float,
+                          dT: float = 0.0, component: int = 0, T_axis: int = 1) -> dict:
+    """A single velocity wave u_component = A sin(k x) on the nodes x_i = 2 pi i / nx
+    (component 0: compressive, 1 or 2: shear), uniform density rho0 and a temperature
+    T = T0 (1 + dT cos(2 pi j / n_T)) that varies along T_axis (1: y, 2: z) only, so
+    the velocity and the temperature are functions of different coordinates. Returns
+    float64 rho, ux, uy, uz, p of shape (nz, ny, nx) and the 1-D temperature profile
+    T_line (input data for diagnostics with closed forms)."""
+    x = np.arange(nx) * 2.0 * math.pi / nx
+    n_T = ny if T_axis == 1 else nz
+    T_line = T0 * (1.0 + dT * np.cos(2.0 * math.pi * np.arange(n_T) / n_T))
+    shape = (nz, ny, nx)
+    u = [np.zeros(shape) for _ in range(3)]
+    u[component] = np.broadcast_to(A * np.sin(k * x), shape).copy()
+    T = np.broadcast_to(T_line[:, None] if T_axis == 1 else T_line[:, None, None], shape)
+    rho = np.full(shape, rho0)
+    return dict(rho=rho, ux=u[0], uy=u[1], uz=u[2], p=rho * T, T_line=T_line)

@@ -328,6 +328,43 @@ def test_step_diag_matches_oracle_on_tgv(lbm, oracle_mod):
     dom.close()
 
 
+@pytest.mark.parametrize("component,T_axis", [(0, 1), (1, 2)])
+def test_diag_closed_forms_on_wave(lbm, component, T_axis):
+    """Both diagnostic paths (lbm_diag, and lbm_step_diag inside the first step) on
+    one velocity wave u_c = A sin(k x) with a temperature varying along another axis
+    (Sutherland viscosity) against the closed forms the oracle is pinned to (Eq. 7:
+    2/3 mbar A^2 (sin(k dx)/dx)^2 compressive, 1/2 mbar A^2 (sin(k dx)/dx)^2 shear;
+    max Mach A / sqrt(gamma T_min); max CFL (A + sqrt(gamma T_max)) dt/dx), at the FP32
+    tolerances of the diagnostics tests."""
+    nx, ny, nz, k, A, rho0, T0, mu, T_ref = 48, 6, 5, 2, 0.3, 1.3, 0.9, 0.037, 0.8
+    p = inputs.tgv_params(16)
+    p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / nx, mu=mu, T_ref=T_ref, sutherland=1)
+    f = inputs.separable_wave_fields(nx, ny, nz, A, k, rho0, T0, 0.35, component, T_axis)
+    S = 0.4042 * T_ref
+    T_line = f["T_line"]
+    mbar = float(np.mean(mu * (T_line / T_ref) ** 1.5 * (T_ref + S) / (T_line + S)))
+    h = p["dx"]
+    g2 = (np.sin(k * h) / h) ** 2
+    gamma = p["gamma"]
+    for path in ("diag", "step_diag"):
+        dom = lbm.Domain(p)
+        dom.init_fields(f["rho"], f["ux"], f["uy"], f["uz"], f["p"])
+        d = dom.diag() if path == "diag" else dom.step_diag(1)
+        dt = dom.info()["dt"]
+        dom.close()
+        if component == 0:
+            assert d["eps_d_raw"] == pytest.approx(2.0 / 3.0 * mbar * A * A * g2, rel=1e-5), path
+            assert abs(d["eps_s_raw"]) < 1e-9 * mbar * A * A * g2, path
+        else:
+            assert d["eps_s_raw"] == pytest.approx(0.5 * mbar * A * A * g2, rel=1e-5), path
+            assert abs(d["eps_d_raw"]) < 1e-9 * mbar * A * A * g2, path
+        assert d["max_mach"] == pytest.approx(A / np.sqrt(gamma * T_line.min()), rel=2e-6), path
+        assert d["max_cfl"] == pytest.approx((A + np.sqrt(gamma * T_line.max())) * dt / h,
+                                             rel=2e-6), path
+        assert d["ek_mean"] == pytest.approx(rho0 * A * A / 4.0, rel=2e-6), path
+        assert d["min_T"] == pytest.approx(T_line.min(), rel=2e-6), path
+
+
 def test_step_diag_reports_non_finite_state(lbm):
     p = inputs.tgv_params(8)
     dom = lbm.Domain(p)

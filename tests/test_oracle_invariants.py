@@ -154,3 +154,62 @@ def test_tgv_initial_diagnostics(oracle_mod):
     assert d["sum_rho"] == pytest.approx(rho.sum(), rel=1e-13)
     assert d["min_T"] == pytest.approx(p0, rel=1e-12)
     assert d["nonfinite"] == 0
+
+
+def _sutherland_printed(T, T_ref, mu):
+    """Sutherland's law in the form printed with the TGV setup (Sec. 3.2):
+    mu (T/T_ref)^{3/2} (T_ref + S) / (T + S) with S = 0.4042 T_ref."""
+    S = 0.4042 * T_ref
+    return mu * (T / T_ref) ** 1.5 * (T_ref + S) / (T + S)
+
+
+@pytest.mark.parametrize("sutherland,dT,component,T_axis", [
+    (0, 0.0, 0, 1),    # constant viscosity, uniform T, compressive wave u_x(x)
+    (1, 0.0, 0, 1),    # Sutherland at a uniform T != T_ref
+    (1, 0.35, 0, 1),   # Sutherland with T varying along y, compressive wave
+    (1, 0.35, 1, 2),   # shear wave u_y(x), T varying along z
+    (1, 0.35, 2, 1),   # shear wave u_z(x), T varying along y
+])
+def test_wave_diagnostics_closed_forms(oracle_mod, sutherland, dT, component, T_axis):
+    """Eq. 7 and the extrema of the diagnostics on a field whose velocity is one wave
+    u_c = A sin(k x) and whose temperature depends only on y or z. The central
+    difference of sin(k x) is cos(k x) sin(k dx)/dx and the grid mean of cos^2 is 1/2,
+    so with mu_local averaged over the temperature profile (mbar):
+      compressive (c = x): 4/3 <mu_local (div u)^2> = 2/3 mbar A^2 (sin(k dx)/dx)^2, no curl;
+      shear (c = y, z):    <mu_local |curl u|^2>   = 1/2 mbar A^2 (sin(k dx)/dx)^2, no div;
+    max Mach = A / sqrt(gamma T_min); max CFL = (A + sqrt(gamma T_max)) dt/dx (|u_c| and
+    T peak in different coordinates, so both maxima meet in one cell);
+    <rho |u|^2 / 2> = rho0 A^2 / 4. A dropped or doubled 4/3, mu_local applied twice
+    (mu = 0.037, so mu^2 != mu), the square of the mean in place of the mean of the
+    square, swapped dissipation channels, a missing gamma or a missing sound speed all
+    fail here."""
+    nx, ny, nz, k, A, rho0, T0, mu, T_ref = 16, 6, 5, 2, 0.3, 1.3, 0.9, 0.037, 0.8
+    p = _tgv_like(nx, ny, nz, mu=mu, sutherland=sutherland, T_ref=T_ref)
+    o = make_oracle(p)
+    f = inputs.separable_wave_fields(nx, ny, nz, A, k, rho0, T0, dT, component, T_axis)
+    o.init_fields(f["rho"], f["ux"], f["uy"], f["uz"], f["p"])
+    d = o.diag()
+    h = p["dx"]
+    g2 = (math.sin(k * h) / h) ** 2
+    T_line = f["T_line"]
+    mbar = float(np.mean(_sutherland_printed(T_line, T_ref, mu))) if sutherland else mu
+    n = nx * ny * nz
+    if component == 0:
+        assert d["eps_d_raw"] == pytest.approx(2.0 / 3.0 * mbar * A * A * g2, rel=1e-12)
+        assert abs(d["eps_s_raw"]) < 1e-20
+    else:
+        assert d["eps_s_raw"] == pytest.approx(0.5 * mbar * A * A * g2, rel=1e-12)
+        assert abs(d["eps_d_raw"]) < 1e-20
+    gamma = p["gamma"]
+    assert d["max_mach"] == pytest.approx(A / math.sqrt(gamma * T_line.min()), rel=1e-12)
+    assert d["max_cfl"] == pytest.approx((A + math.sqrt(gamma * T_line.max())) * o.dt / h,
+                                         rel=1e-12)
+    assert d["ek_mean"] == pytest.approx(rho0 * A * A / 4.0, rel=1e-12)
+    assert d["min_T"] == pytest.approx(T_line.min(), rel=1e-12)
+    assert d["min_rho"] == pytest.approx(rho0, rel=1e-14)
+    assert d["sum_rho"] == pytest.approx(rho0 * n, rel=1e-14)
+    E_mean = rho0 * float(np.mean(T_line)) / (gamma - 1.0) + rho0 * A * A / 4.0
+    assert d["sum_E"] == pytest.approx(E_mean * n, rel=1e-13)
+    for key in ("sum_mx", "sum_my", "sum_mz"):
+        assert abs(d[key]) < 1e-12
+    assert d["nonfinite"] == 0

@@ -50,3 +50,30 @@ def test_parseval_and_random_gradients():
     assert np.allclose(g, du, atol=1e-10)
     _, E = spectral.energy_spectrum(u)
     assert E.sum() == pytest.approx(0.5 * np.mean((u ** 2).sum(0)), rel=1e-12)
+
+
+@pytest.mark.parametrize("component,T_axis", [(0, 1), (0, 2), (1, 2), (2, 1)])
+def test_wave_dissipation_closed_forms(component, T_axis):
+    """Spectral Eq. 7 on one velocity wave u_c = A sin(k x) with a temperature that
+    depends only on y or z (Sutherland viscosity): the spectral derivative is exact,
+    <cos^2> = 1/2 on the grid, and mu_local averages over the temperature profile, so
+    eps_d = 4/3 mbar A^2 k^2 / 2 / rho_ref for the compressive wave (c = x) and
+    eps_s = mbar A^2 k^2 / 2 / rho_ref for a shear wave; the other rate is zero. mbar
+    uses the form of Sutherland's law printed with the TGV setup (Sec. 3.2),
+    mu (T/T_ref)^{3/2} (T_ref + S)/(T + S), S = 0.4042 T_ref."""
+    from paper_2608_13437_gb300 import inputs
+    nx, ny, nz, k, A, T0, mu, T_ref, rho_ref = 16, 6, 8, 3, 0.4, 0.9, 0.037, 0.8, 1.7
+    f = inputs.separable_wave_fields(nx, ny, nz, A, k, 1.0, T0, 0.35, component, T_axis)
+    T = f["p"] / f["rho"]
+    S = 0.4042 * T_ref
+    mbar = float(np.mean(mu * (f["T_line"] / T_ref) ** 1.5 * (T_ref + S) / (f["T_line"] + S)))
+    # dissipation() takes each axis to span 2 pi; only x carries a velocity gradient,
+    # so the y and z extents do not enter
+    u = np.stack([f["ux"], f["uy"], f["uz"]])
+    es, ed = spectral.dissipation(u, T, mu, T_ref, True, rho_ref)
+    if component == 0:
+        assert ed == pytest.approx(4.0 / 3.0 * mbar * A * A * k * k / 2.0 / rho_ref, rel=1e-12)
+        assert abs(es) < 1e-20
+    else:
+        assert es == pytest.approx(mbar * A * A * k * k / 2.0 / rho_ref, rel=1e-12)
+        assert abs(ed) < 1e-20
