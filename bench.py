@@ -63,8 +63,11 @@ def kernel_hash():
 
 
 def traffic_per_launch(store, ncell):
-    """DRAM bytes per launch from the committed ncu summary, scaled by cells; None
-    when the kernel sources changed since the counters were taken."""
+    """DRAM bytes per launch at ncell cells from the committed ncu counters of a smaller
+    capture: the reads per cell scale with the cells, and the in-place step writes back
+    every line it reads once its state exceeds L2 (at the small capture part of the
+    writes is still dirty in L2 when the kernel ends), so writes = reads. None when the
+    kernel sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
         with open(path) as fh:
@@ -74,7 +77,7 @@ def traffic_per_launch(store, ncell):
     ent = d.get(store)
     if not ent or ent.get("kernel_hash") != kernel_hash():
         return None
-    return ent["dram_bytes_per_cell"] * ncell
+    return 2.0 * ent["dram_read_bytes_per_cell"] * ncell
 
 
 class ClockSampler:
@@ -177,13 +180,16 @@ def time_oracle(n_global, side, steps, warmup, threads=None):
     return side ** 3 * steps / dt / 1e6, dt, get_threads()
 
 
+CPU_WINDOW = 160  # side of the oracle's window of the TGV, as in the reference arm
+
+
 def cpu_baseline(n_global, budget_s=15.0):
-    """Bounded sample: calibrate on 32^3, then time a 128^3 window for as many steps
-    as fit in about budget_s seconds."""
+    """Bounded sample: calibrate on 32^3, then time a 160^3 window (the reference arm's
+    largest window) for as many steps as fit in about budget_s seconds."""
     rate, _, thr = time_oracle(n_global, 32, 2, 0)
-    side = 128
+    side = CPU_WINDOW
     steps = max(1, min(50, int(budget_s * rate * 1e6 / side ** 3)))
-    mlups, secs, thr = time_oracle(n_global, side, steps, 0)
+    mlups, secs, thr = time_oracle(n_global, side, steps, 1)
     # the same code on one core, on a 64^3 window for about 3 s
     from oracle.oracle import set_threads
     r1, _, _ = time_oracle(n_global, 32, 1, 0, threads=1)
@@ -192,9 +198,20 @@ def cpu_baseline(n_global, budget_s=15.0):
     set_threads(thr)
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
             "sample": f"FP64 oracle, {side}^3 window of the {n_global}^3 TGV, {steps} steps "
-                      f"({secs:.1f} s), OpenMP over z-planes",
+                      f"({secs:.1f} s) after 1 warm-up step, OpenMP over z-planes, in a fresh "
+                      "process started before any CUDA work (no torch loaded)",
             "single_core": {"value": round(one, 3), "unit": "MLUPS",
                             "sample": f"64^3 window, {s1} steps ({secs1:.1f} s), 1 thread"}}
+
+
+def cpu_baseline_subprocess(n_global):
+    """cpu_baseline() in a fresh interpreter that loads neither torch nor CUDA, run to
+    completion before the GPU legs start, so the oracle has the host cores to itself."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+                        "--n", str(n_global)], capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"CPU baseline failed:\n{r.stdout}\n{r.stderr}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -350,7 +367,12 @@ def run_gpu(args):
     dom = lbm.Domain(p, store=args.store)
     dom.init_tgv(1.0, 1.25, 1.0)
     tune = dom.autotune(pairs_per_trial=3)   # advances the state: re-init below
-    dom.init_tgv(1.0, 1.25, 1.0)
+    ev_init = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev_init[0].record(dom.stream)
+    dom.init_tgv(1.0, 1.25, 1.0)            # FP32 initial equilibrium on the device
+    ev_init[1].record(dom.stream)
+    torch.cuda.synchronize()
+    init_tgv_ms = ev_init[0].elapsed_time(ev_init[1])
     ms_total, clocks = time_steps(torch, dom, args.steps, args.warmup, dist,
                                   sampler_index=dev if rank == 0 else None)
     ms_max = reduce_max(ms_total, dist, "cuda")
@@ -396,7 +418,8 @@ def run_gpu(args):
     ev[3].record(dom.stream)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
-    phases = {"init_from_host_ms": round(ev[0].elapsed_time(ev[1]), 2),
+    phases = {"init_tgv_ms": round(init_tgv_ms, 2),
+              "init_from_host_ms": round(ev[0].elapsed_time(ev[1]), 2),
               "steps_with_diagnostics_ms": round(ev[1].elapsed_time(ev[2]), 2),
               "moments_to_host_ms": round(ev[2].elapsed_time(ev[3]), 2)}
     e2e = {"value": round(job_value(world, ncell, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
@@ -452,7 +475,13 @@ def run_gpu(args):
         variants["batch64_f16_stochastic_rounding"] = batch_leg(
             torch, lbm, inputs, min(args.steps, 200), args.warmup, store="f16", sround=1)
 
-    cpu = cpu_baseline(n) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    cpu = args.cpu
+    if cpu is not None and not args.no_variants:
+        # the same oracle in this process after the GPU legs, for comparison only
+        in_proc, secs_ip, thr_ip = time_oracle(n, CPU_WINDOW, 4, 1)
+        cpu["in_gpu_process_after_gpu_legs"] = {
+            "value": round(in_proc, 3), "unit": "MLUPS", "cores": thr_ip,
+            "sample": f"{CPU_WINDOW}^3 window, 4 steps ({secs_ip:.1f} s)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
@@ -491,14 +520,22 @@ def main():
     ap.add_argument("--only-batch", type=int, default=0, metavar="K",
                     help="run only the batched-mode leg on the first K seeded domains "
                          "(storage from --store)")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.cpu_baseline_only:  # the child process of cpu_baseline_subprocess
+        print(json.dumps(cpu_baseline(args.n)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
     from paper_2608_13437_gb300 import build
     build.build()
+    world, rank, _ = dist_setup()
+    args.cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.only_batch:
+        args.cpu = cpu_baseline_subprocess(args.n)
     if args.only_batch:
         import torch
 

@@ -52,7 +52,8 @@ typedef enum {
   LBM_OK = 0,
   LBM_E_INVAL = 1,      /* bad argument or parameter */
   LBM_E_NOMEM = 2,      /* device or host allocation failed */
-  LBM_E_CUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  LBM_E_CUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error), or
+                           the handle's device could not be made current */
   LBM_E_NONFINITE = 4,  /* a non-finite moment was detected; sticky until re-init */
   LBM_E_STATE = 5,      /* call not valid in the current state (e.g. step before init) */
   LBM_E_IO = 6,         /* checkpoint file could not be read or written, or is corrupt */
@@ -108,9 +109,8 @@ typedef struct {
                             down at random with the probabilities that make the rounding
                             unbiased (random bits from the cell's index and state, so the
                             result is reproducible); 0 rounds to nearest (default). The
-                            staged kernel forms round to nearest only (the autotuner
-                            then chooses among the others); a batch takes one mode for
-                            all its domains */
+                            staged kernel forms round to nearest only; a batch takes one
+                            mode for all its domains */
   int use_graphs;        /* 1: lbm_step replays captured CUDA graphs of whole step pairs */
   void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
   void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
@@ -137,6 +137,7 @@ typedef struct {
                                2 stages with <= 128 (3), 3 stages with <= 170 (4) */
   int prefetch_tiles;       /* L2 prefetch distance of variants 0 and 1 on whole-tile rows
                                (see lbm_set_prefetch); 0 = off */
+  int device;               /* CUDA device ordinal the handle is bound to (see lbm_create) */
 } lbm_info_t;
 
 /* Diagnostics (Sec. 3.2, Eq. 7). Sums and extrema in FP64 over all cells.
@@ -174,7 +175,10 @@ size_t lbm_population_bytes(const lbm_params* p);
  * times, allocates the device state on the current CUDA device (LBM_E_NOMEM if it
  * does not fit) and returns an uninitialised handle in *out. The state is one
  * population buffer updated in place; nothing of size O(cells) is allocated
- * besides it until lbm_diag is first called. */
+ * besides it until lbm_diag is first called. The handle is bound to that device
+ * (lbm_info_t.device): every later call on it makes the device current while it
+ * runs and restores the caller's current device before returning, so one thread can
+ * drive handles on several GPUs. cuda_stream and pop_buffer must belong to it. */
 lbm_status lbm_create(const lbm_params* p, lbm_handle** out);
 
 /* Releases everything the handle allocated (not borrowed buffers or streams).
@@ -279,8 +283,9 @@ lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out);
  * library (about 4.2 MiB on every device that loads the library, kept until the
  * process exits), so it handles domains of at most 262144 cells (64^3) and returns
  * LBM_E_INVAL for larger ones. The first call on a device looks up the array's
- * device address (with that device current); make that first call before any
- * stream capture. Calls share the array: two calls whose kernels overlap on the
+ * device address (with the handle's device made current) and keeps it; make that
+ * first call before any stream capture (the kept address does not survive
+ * cudaDeviceReset). Calls share the array: two calls whose kernels overlap on the
  * GPU race, so serialise them. Synchronises the handle's stream. */
 lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out);
 
@@ -308,9 +313,10 @@ lbm_status lbm_load(lbm_handle* h, const char* path);
 
 /* Times the step kernel for each candidate form (variants 0 and 1 at blocks of 64
  * and 128 threads, each with L2 prefetch distances 0, 512, 1024 and 2048 tiles on
- * whole-tile rows; the staged variants 2-4 where the domain allows them) on whole
- * step pairs with CUDA events on the handle's stream, and keeps the fastest in the
- * handle; returns it in *out if out != NULL. Needs an initialised state
+ * whole-tile rows: at most 16 candidates; the staged variants 2-4, measured slower
+ * everywhere, only through lbm_set_kernel_config) on whole step pairs with CUDA events
+ * on the handle's stream, and keeps the fastest in the handle; returns it in *out if
+ * out != NULL. Needs an initialised state
  * (LBM_E_STATE otherwise); each candidate runs on the live state, so the state
  * advances by an even number of steps: re-init before the run you keep. */
 lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
@@ -380,7 +386,8 @@ lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int sr
 
 /* ---- many independent domains (batched mode) -------------------------------------
  * n periodic domains with their own sizes and parameters (one storage type for all,
- * F32, F16 or BF16), stored in one buffer. lbm_batch_step advances all of them by one step per persistent launch
+ * F32, F16 or BF16), stored in one buffer on the device current at lbm_batch_create,
+ * to which the batch is bound as a handle is (see lbm_create). lbm_batch_step advances all of them by one step per persistent launch
  * (grid = the resident blocks of the GPU; each warp takes items of consecutive
  * 32-cell tiles across all domains, the domain constants staged in shared memory),
  * replayed from a CUDA graph; lbm_batch_step_sequential issues one plain launch per

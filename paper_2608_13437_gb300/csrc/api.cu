@@ -149,6 +149,7 @@ cudaError_t launch_step_diag(const DomainConst& P, int store, int parity, void* 
 
 struct lbm_handle {
   lbm_params prm;
+  int device = 0;              // CUDA device current at lbm_create; every call runs there
   DomainConst P;
   double dt = 0, tau_R = 0, tau_q = 0;
   double rho_ref = 0, E_ref = 0;
@@ -161,6 +162,7 @@ struct lbm_handle {
   unsigned* flag = nullptr;    // non-finite flag (device)
   unsigned* maxbits = nullptr; // per-field max |deviation| (device)
   double* sums = nullptr;      // field means (device)
+  float* trig = nullptr;       // TGV table: sin, cos, cos 2x of the nodes of each axis (device)
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;  // capture-only stream
   long long step = 0;
@@ -270,23 +272,18 @@ void reset_scales(lbm_handle* h) {
   }
 }
 
-// Runs both init passes for an initial state: Q_ref must be set beforehand.
-lbm_status run_init(lbm_handle* h, InitSpec& sp) {
-  h->P.rho_ref = (float)h->rho_ref;
-  h->P.E_ref = (float)h->E_ref;
-  // Q_ref as actually used on the device (float).
+// The storage reference Q_ref = (rho_ref, 0, 0, 0, E_ref, 0...) as the device uses it
+// (FP32); the handle reports the same values.
+void set_reference(lbm_handle* h, double rho_ref, double E_ref) {
+  h->P.rho_ref = (float)rho_ref;
+  h->P.E_ref = (float)E_ref;
   h->rho_ref = (double)h->P.rho_ref;
   h->E_ref = (double)h->P.E_ref;
+}
+
+// Runs both init passes for an initial state: Q_ref must be set beforehand.
+lbm_status run_init(lbm_handle* h, InitSpec& sp) {
   reset_scales(h);
-  sp.gamma = h->prm.gamma;
-  sp.mu = h->prm.mu;
-  sp.kappa = h->prm.kappa;
-  sp.tau_R = h->tau_R;
-  sp.tau_q = h->tau_q;
-  sp.inv_T_ref = 1.0 / h->prm.T_ref;
-  sp.c = h->prm.dx / h->dt;
-  sp.dx = h->prm.dx;
-  sp.sutherland = h->prm.sutherland;
   if (h->prm.store == LBM_STORE_F16) {
     LBM_CUDA(cudaMemsetAsync(h->maxbits, 0, kF * sizeof(unsigned), h->stream));
     LBM_CUDA(launch_init(h->P, h->prm.store, sp, 0, h->pop, h->ghost, h->maxbits, h->stream));
@@ -350,9 +347,18 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
   *out = nullptr;
   lbm_status s = validate(p);
   if (s != LBM_OK) return s;
+  int device = 0;
+  {
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_E_CUDA, "no current CUDA device: %s", cudaGetErrorString(e));
+    }
+  }
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return fail(LBM_E_NOMEM, "host allocation failed");
   h->prm = *p;
+  h->device = device;
   derive(p, &h->dt, &h->tau_R, &h->tau_q);
   if (!(h->dt > 0) || !std::isfinite(h->dt)) {
     delete h;
@@ -388,7 +394,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
   const size_t ghost_bytes = sizeof(float) * 2 * kF * (size_t)p->ny * p->nz;
   if (cudaMalloc(&h->ghost, ghost_bytes) != cudaSuccess || cudaMalloc(&h->flag, 64) != cudaSuccess ||
       cudaMalloc(&h->maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&h->sums, kFieldSumDoubles * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&h->sums, kFieldSumDoubles * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->trig, sizeof(float) * tgv_table_floats(p->nx, p->ny, p->nz)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of small device buffers failed"));
   }
@@ -402,6 +409,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
 
 lbm_status lbm_destroy(lbm_handle* h) {
   if (!h) return LBM_OK;
+  DeviceScope scope(h->device);  // best effort: release what can be released either way
   if (h->stream || h->pop) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   if (h->own_pop && h->pop) cudaFree(h->pop);
@@ -409,6 +417,7 @@ lbm_status lbm_destroy(lbm_handle* h) {
   if (h->flag) cudaFree(h->flag);
   if (h->maxbits) cudaFree(h->maxbits);
   if (h->sums) cudaFree(h->sums);
+  if (h->trig) cudaFree(h->trig);
   if (h->ufield) cudaFree(h->ufield);
   if (h->partials) cudaFree(h->partials);
   if (h->dout) cudaFree(h->dout);
@@ -438,23 +447,26 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out) {
   out->block_x = effective_block(h);
   out->variant = h->variant;
   out->prefetch_tiles = h->P.pf_tiles;
+  out->device = h->device;
   return LBM_OK;
 }
 
 lbm_status lbm_init_tgv(lbm_handle* h, double U0, double M0, double rho0) {
   Range range_("lbm_init_tgv");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  LBM_ON_DEVICE(h->device);
   if (!(std::isfinite(U0) && finite_pos(M0) && finite_pos(rho0)))
     return fail(LBM_E_INVAL, "TGV needs finite U0 and M0, rho0 > 0");
-  InitSpec sp{};
-  sp.kind = 0;
-  sp.U0 = U0;
-  sp.M0 = M0;
-  sp.rho0 = rho0;
   const double p0 = rho0 * U0 * U0 / (h->prm.gamma * M0 * M0);
   if (!finite_pos(p0)) return fail(LBM_E_INVAL, "TGV background pressure must be > 0 (U0 != 0)");
-  h->rho_ref = rho0;
-  h->E_ref = p0 / (h->prm.gamma - 1.0);
+  set_reference(h, rho0, p0 / (h->prm.gamma - 1.0));
+  InitSpec sp;
+  std::vector<float> table;
+  tgv_spec(h->P, h->prm.gamma, U0, M0, rho0, h->prm.dx, &sp, &table);
+  // pageable source: the call returns once the table is staged, in stream order
+  LBM_CUDA(cudaMemcpyAsync(h->trig, table.data(), sizeof(float) * table.size(),
+                           cudaMemcpyHostToDevice, h->stream));
+  sp.trig = h->trig;
   return run_init(h, sp);
 }
 
@@ -462,21 +474,15 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
                             const double right[3]) {
   Range range_("lbm_init_riemann");
   if (!h || !left || !right) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (axis < 0 || axis > 2) return fail(LBM_E_INVAL, "axis must be 0, 1 or 2");
   for (int j = 0; j < 3; ++j)
     if (!std::isfinite(left[j]) || !std::isfinite(right[j])) return fail(LBM_E_INVAL, "non-finite state");
   if (!(left[0] > 0 && right[0] > 0 && left[2] > 0 && right[2] > 0))
     return fail(LBM_E_INVAL, "densities and pressures must be > 0");
-  InitSpec sp{};
-  sp.kind = 1;
-  sp.axis = axis;
-  sp.split = i_split;
-  for (int j = 0; j < 3; ++j) {
-    sp.left[j] = left[j];
-    sp.right[j] = right[j];
-  }
-  h->rho_ref = right[0];
-  h->E_ref = right[2] / (h->prm.gamma - 1.0) + 0.5 * right[0] * right[1] * right[1];
+  set_reference(h, right[0], right[2] / (h->prm.gamma - 1.0) + 0.5 * right[0] * right[1] * right[1]);
+  InitSpec sp;
+  riemann_spec(h->P, h->prm.gamma, axis, i_split, left, right, &sp);
   return run_init(h, sp);
 }
 
@@ -501,6 +507,7 @@ static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on
                                    int kind, int nfield) {
   Range range_("lbm_init_fields");
   if (!h || !fields) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
   const size_t bytes = (size_t)nfield * h->ncell * (dtype == LBM_DT_F64 ? 8 : 4);
   void* dev = const_cast<void*>(fields);
@@ -520,11 +527,8 @@ static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on
     }
     dev = tmp;
   }
-  InitSpec sp{};
-  sp.kind = kind;
-  sp.fields = dev;
-  sp.fields_f64 = dtype == LBM_DT_F64;
-  sp.gamma = h->prm.gamma;
+  InitSpec sp;
+  fields_spec(h->prm.gamma, kind, dev, dtype == LBM_DT_F64, &sp);
   lbm_status st = LBM_OK;
   double sums[2] = {0, 0};
   cudaError_t e = launch_field_means(h->P, sp, h->sums, h->stream);
@@ -533,12 +537,13 @@ static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on
   if (e != cudaSuccess) {
     st = fail(LBM_E_CUDA, "field means failed: %s", cudaGetErrorString(e));
   } else {
-    h->rho_ref = sums[0] / (double)h->ncell;
-    h->E_ref = sums[1] / (double)h->ncell;
-    if (!std::isfinite(h->rho_ref) || !std::isfinite(h->E_ref))
+    const double rho_ref = sums[0] / (double)h->ncell, E_ref = sums[1] / (double)h->ncell;
+    if (!std::isfinite(rho_ref) || !std::isfinite(E_ref)) {
       st = fail(LBM_E_INVAL, "initial fields contain non-finite values");
-    else
+    } else {
+      set_reference(h, rho_ref, E_ref);
       st = run_init(h, sp);
+    }
   }
   if (tmp) cudaFree(tmp);
   return st;
@@ -555,6 +560,7 @@ lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int d
 lbm_status lbm_step(lbm_handle* h, int n) {
   Range range_("lbm_step");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  LBM_ON_DEVICE(h->device);
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
@@ -594,6 +600,7 @@ lbm_status lbm_step(lbm_handle* h, int n) {
 
 lbm_status lbm_synchronize(lbm_handle* h) {
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  LBM_ON_DEVICE(h->device);
   unsigned flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -618,6 +625,7 @@ static lbm_status ensure_stage(lbm_handle* h) {
 lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, int dtype) {
   Range range_("lbm_moments");
   if (!h || !dst) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (which != LBM_MOM_Q && which != LBM_MOM_PRIM) return fail(LBM_E_INVAL, "bad moment set");
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
   const int nf = which == LBM_MOM_Q ? kF : 6;
@@ -657,6 +665,7 @@ lbm_status lbm_moments(lbm_handle* h, int which, void* dst, int dst_on_device, i
 
 lbm_status lbm_sensor(lbm_handle* h, void* dst, int dst_on_device, int dtype) {
   if (!h || !dst) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
   const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
   const int parity = (int)(h->step & 1);
@@ -708,8 +717,12 @@ static lbm_status ensure_diag_scratch(lbm_handle* h) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace lbm {
+
 // Fills *out from the reduced values r[0..kDiagA+2) of the state after `step` steps.
-static lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, long long step,
+lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, long long step,
                               lbm_diag_t* out) {
   const double n = (double)h->ncell;
   out->step = (double)step;
@@ -734,9 +747,14 @@ static lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, lon
   return LBM_OK;
 }
 
+}  // namespace lbm
+
+extern "C" {
+
 lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
   Range range_("lbm_diag");
   if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   lbm_status st = ensure_diag_scratch(h);
   if (st != LBM_OK) return st;
   double r[16] = {0};
@@ -752,6 +770,7 @@ lbm_status lbm_diag(lbm_handle* h, lbm_diag_t* out) {
 lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
   Range range_("lbm_step_diag");
   if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (n < 1) return fail(LBM_E_INVAL, "n must be >= 1");
   if (!h->initialized) return fail(LBM_E_STATE, "lbm_step_diag before an init");
   if (h->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
@@ -801,6 +820,7 @@ lbm_status lbm_step_diag(lbm_handle* h, int n, lbm_diag_t* out) {
 
 static lbm_status pop_transfer(lbm_handle* h, void* buf, int on_device, int dtype, bool get) {
   if (!h || !buf) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64 && dtype != LBM_DT_NATIVE)
     return fail(LBM_E_INVAL, "bad dtype");
   const size_t es = dtype == LBM_DT_F64 ? 8 : (dtype == LBM_DT_F32 ? 4 : elem_size(h->prm.store));
@@ -847,6 +867,7 @@ lbm_status lbm_populations_set(lbm_handle* h, const void* src, int src_on_device
 static lbm_status plane_transfer(lbm_handle* h, int z, int slot, void* buf, int on_device, bool set) {
   Range range_("lbm_plane");
   if (!h || !buf) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (z < 0 || z >= h->prm.nz) return fail(LBM_E_INVAL, "plane z = %d outside [0, %d)", z, h->prm.nz);
   if (slot < 0 || slot >= kQ) return fail(LBM_E_INVAL, "slot %d outside [0, 7)", slot);
   const size_t bytes = elem_size(h->prm.store) * kF * (size_t)h->prm.nx * h->prm.ny;
@@ -881,6 +902,7 @@ lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int sr
 lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
   Range range_("lbm_autotune");
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  LBM_ON_DEVICE(h->device);
   if (!h->initialized) return fail(LBM_E_STATE, "autotune needs an initialised state");
   if (h->nonfinite || h->stalled) return fail(LBM_E_STATE, "autotune on a failed state; re-init");
   if (pairs_per_trial < 1) pairs_per_trial = 4;
@@ -895,8 +917,11 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
       if (b <= 32 * ((h->P.nx + 31) / 32) || b == 64)
         for (int pf : {0, 512, 1024, 2048})
           if (pf == 0 || rows) cands.push_back({v, b, pf});
-  if (staged_eligible(h->P))
-    for (int v = kFirstStagedVariant; v <= kLastStagedVariant; ++v) cands.push_back({v, 128, 0});
+  // The staged forms (variants 2-4) are not candidates: measured slower than the plain
+  // forms at every size and storage type (their shared-memory pipeline costs more
+  // instructions per cell than it saves in latency, and the L2 prefetch hides the
+  // same latency for 1-3 instructions per warp). lbm_set_kernel_config still selects
+  // them explicitly.
   cudaEvent_t a, b;
   LBM_CUDA(cudaEventCreate(&a));
   LBM_CUDA(cudaEventCreate(&b));
@@ -970,6 +995,7 @@ lbm_status lbm_test_skip_copy(lbm_handle* h) {
 
 lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
   if (!h) return fail(LBM_E_INVAL, "handle is NULL");
+  LBM_ON_DEVICE(h->device);
   if (variant < 0 || variant > kLastStagedVariant) return fail(LBM_E_INVAL, "variant must be 0 to 4");
   if (variant >= kFirstStagedVariant) {
     if (!staged_eligible(h->P))
@@ -1031,6 +1057,7 @@ struct CkptHeader {
 
 lbm_status lbm_save(lbm_handle* h, const char* path) {
   if (!h || !path) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   if (!h->initialized) return fail(LBM_E_STATE, "nothing to save before an init");
   CkptHeader hd{};
   std::memcpy(hd.magic, "LBMCKPT1", 8);
@@ -1066,6 +1093,7 @@ lbm_status lbm_save(lbm_handle* h, const char* path) {
 
 lbm_status lbm_load(lbm_handle* h, const char* path) {
   if (!h || !path) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(h->device);
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(LBM_E_IO, "cannot open %s", path);
   CkptHeader hd{};
@@ -1116,8 +1144,7 @@ lbm_status lbm_load(lbm_handle* h, const char* path) {
 
 // ---------------------------------------------------------------- internal view
 // Read access to a handle's device state for other translation units of the
-// library (the fixed-scratch diagnostics in diag_static.cu), plus the one latch
-// they may set.
+// library (the fixed-scratch diagnostics in diag_static.cu).
 namespace lbm {
 
 HandleView handle_view(lbm_handle* h) {
@@ -1131,15 +1158,8 @@ HandleView handle_view(lbm_handle* h) {
   v.flag = h->flag;
   v.stream = h->stream;
   v.ncell = h->ncell;
+  v.device = h->device;
   return v;
 }
-
-void latch_nonfinite(lbm_handle* h) { h->nonfinite = true; }
-
-void latch_step_flag(lbm_handle* h, unsigned flag) { latch_flag(h, flag); }
-
-bool stall_latched(const lbm_handle* h) { return h->stalled; }
-
-bool nonfinite_latched(const lbm_handle* h) { return h->nonfinite; }
 
 }  // namespace lbm

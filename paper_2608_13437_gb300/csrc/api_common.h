@@ -19,6 +19,43 @@ struct Range {
   Range& operator=(const Range&) = delete;
 };
 
+// Makes `device` the calling thread's current CUDA device for the lifetime of the
+// object and restores the caller's current device afterwards, so every entry point
+// issues its work in the context of the device its handle was created on, whatever
+// device the caller has current. ok() is false if either device query or switch
+// failed (the message is then in error()).
+class DeviceScope {
+ public:
+  explicit DeviceScope(int device) {
+    err_ = cudaGetDevice(&prev_);
+    if (err_ == cudaSuccess && prev_ != device) {
+      err_ = cudaSetDevice(device);
+      switched_ = err_ == cudaSuccess;
+    }
+    if (err_ != cudaSuccess) cudaGetLastError();
+  }
+  ~DeviceScope() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return err_ == cudaSuccess; }
+  const char* error() const { return cudaGetErrorString(err_); }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool switched_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+
+// Opens a DeviceScope for `dev` and returns LBM_E_CUDA from the enclosing entry point
+// if the device cannot be made current.
+#define LBM_ON_DEVICE(dev)                                                                   \
+  ::lbm::DeviceScope lbm_device_scope_(dev);                                                 \
+  if (!lbm_device_scope_.ok())                                                              \
+  return ::lbm::fail(LBM_E_CUDA, "cannot make device %d current: %s", (int)(dev),            \
+                     lbm_device_scope_.error())
+
 extern thread_local std::string g_last_error;
 lbm_status fail(lbm_status s, const char* fmt, ...);
 size_t elem_size(int store);
@@ -41,11 +78,13 @@ struct HandleView {
   unsigned* flag;
   cudaStream_t stream;
   long long ncell;
+  int device;  // CUDA device the handle was created on
 };
 HandleView handle_view(lbm_handle* h);
-void latch_nonfinite(lbm_handle* h);
-bool nonfinite_latched(const lbm_handle* h);
-void latch_step_flag(lbm_handle* h, unsigned flag);  // bit 0 non-finite, bit 1 stalled copy
-bool stall_latched(const lbm_handle* h);
+// Fills *out from the reduced diagnostic values r[0..kDiagA + 2) of the state after
+// `step` steps, latches the step flag and the non-finite count, and returns the
+// handle's sticky status (LBM_E_TIMEOUT, LBM_E_NONFINITE or LBM_OK).
+lbm_status finish_diag(lbm_handle* h, const double* r, unsigned flag, long long step,
+                       lbm_diag_t* out);
 
 }  // namespace lbm

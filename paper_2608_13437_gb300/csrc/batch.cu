@@ -144,6 +144,7 @@ using lbm::batch_kernels::k_batch_step;
 
 struct lbm_batch {
   int n = 0;
+  int device = 0;              // CUDA device current at lbm_batch_create; every call runs there
   std::vector<lbm_params> prm;
   std::vector<DomainConst> P;
   std::vector<double> dt, tau_R, tau_q, rho_ref, E_ref;
@@ -166,6 +167,7 @@ struct lbm_batch {
   size_t smem = 0;
   unsigned* flag = nullptr;
   float* ghost = nullptr;  // unused by periodic domains; a valid pointer for the plain kernel
+  float* trig = nullptr;   // TGV table of the domain being initialised (largest domain's size)
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g_pair = nullptr;
@@ -351,6 +353,14 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     b->total_cells += P.ncell;
   }
   b->stream = static_cast<cudaStream_t>(params[0].cuda_stream);
+  {  // the first CUDA call: everything above is validated on the host
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return fail(LBM_E_CUDA, "no current CUDA device: %s", cudaGetErrorString(e));
+    }
+  }
   auto cleanup = [&](lbm_status st) {
     lbm_batch_destroy(b);
     return st;
@@ -377,12 +387,16 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
     }
   }
   if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
+  size_t max_table = 0;
+  for (int d = 0; d < n; ++d)
+    max_table = std::max(max_table, tgv_table_floats(b->P[d].nx, b->P[d].ny, b->P[d].nz));
   if (cudaMalloc(&b->d_consts, sizeof(DomainConst) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pops, sizeof(void*) * n) != cudaSuccess ||
       cudaMalloc(&b->d_maxbits, 64 + kF * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&b->d_tiles, sizeof(uint2) * tiles.size()) != cudaSuccess ||
       cudaMalloc(&b->d_counter, 64) != cudaSuccess ||
-      cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess) {
+      cudaMalloc(&b->flag, 64) != cudaSuccess || cudaMalloc(&b->ghost, 256) != cudaSuccess ||
+      cudaMalloc(&b->trig, sizeof(float) * max_table) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_E_NOMEM, "cudaMalloc of batch tables failed"));
   }
@@ -402,6 +416,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
 
 lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (!b) return LBM_OK;
+  DeviceScope scope(b->device);  // best effort: release what can be released either way
   cudaStreamSynchronize(b->stream);
   if (b->g_pair) cudaGraphExecDestroy(b->g_pair);
   if (b->pool) cudaFree(b->pool);
@@ -412,6 +427,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->d_maxbits) cudaFree(b->d_maxbits);
   if (b->flag) cudaFree(b->flag);
   if (b->ghost) cudaFree(b->ghost);
+  if (b->trig) cudaFree(b->trig);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return LBM_OK;
@@ -419,6 +435,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
 
 lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, const double* rho0) {
   if (!b || !U0 || !M0 || !rho0) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(b->device);
   for (int d = 0; d < b->n; ++d) {
     const lbm_params& p = b->prm[d];
     if (!(std::isfinite(U0[d]) && finite_pos(M0[d]) && finite_pos(rho0[d])))
@@ -429,20 +446,13 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
     b->P[d].E_ref = (float)(p0 / (p.gamma - 1.0));
     b->rho_ref[d] = (double)b->P[d].rho_ref;
     b->E_ref[d] = (double)b->P[d].E_ref;
-    InitSpec sp{};
-    sp.kind = 0;
-    sp.U0 = U0[d];
-    sp.M0 = M0[d];
-    sp.rho0 = rho0[d];
-    sp.gamma = p.gamma;
-    sp.mu = p.mu;
-    sp.kappa = p.kappa;
-    sp.tau_R = b->tau_R[d];
-    sp.tau_q = b->tau_q[d];
-    sp.inv_T_ref = 1.0 / p.T_ref;
-    sp.c = p.dx / b->dt[d];
-    sp.dx = p.dx;
-    sp.sutherland = p.sutherland;
+    InitSpec sp;
+    std::vector<float> table;
+    tgv_spec(b->P[d], p.gamma, U0[d], M0[d], rho0[d], p.dx, &sp, &table);
+    // pageable source: returns once staged, after the previous domain's kernels
+    LBM_CUDA(cudaMemcpyAsync(b->trig, table.data(), sizeof(float) * table.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    sp.trig = b->trig;
     for (int k = 0; k < kF; ++k) b->P[d].scale[k] = b->P[d].inv_scale[k] = 1.0f;
     if (b->store == LBM_STORE_F16) {  // per-field scale max|f - w Q_ref| / 1024, as for one domain
       LBM_CUDA(cudaMemsetAsync(b->d_maxbits, 0, kF * sizeof(unsigned), b->stream));
@@ -473,6 +483,7 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
 lbm_status lbm_batch_step(lbm_batch* b, int n) {
   Range range_("lbm_batch_step");
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
+  LBM_ON_DEVICE(b->device);
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!b->initialized) return fail(LBM_E_STATE, "lbm_batch_step before an init");
   if (b->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
@@ -498,6 +509,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
 lbm_status lbm_batch_step_sequential(lbm_batch* b, int n) {
   Range range_("lbm_batch_step_sequential");
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
+  LBM_ON_DEVICE(b->device);
   if (n < 0) return fail(LBM_E_INVAL, "n must be >= 0");
   if (!b->initialized) return fail(LBM_E_STATE, "lbm_batch_step_sequential before an init");
   if (b->nonfinite) return fail(LBM_E_NONFINITE, "non-finite moments were detected earlier");
@@ -515,6 +527,7 @@ lbm_status lbm_batch_step_sequential(lbm_batch* b, int n) {
 
 lbm_status lbm_batch_synchronize(lbm_batch* b) {
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
+  LBM_ON_DEVICE(b->device);
   unsigned flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, b->flag, sizeof(flag), cudaMemcpyDeviceToHost, b->stream));
   LBM_CUDA(cudaStreamSynchronize(b->stream));
@@ -526,6 +539,7 @@ lbm_status lbm_batch_synchronize(lbm_batch* b) {
 lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int dst_on_device,
                              int dtype) {
   if (!b || !dst) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(b->device);
   if (domain < 0 || domain >= b->n) return fail(LBM_E_INVAL, "domain index out of range");
   if (which != LBM_MOM_Q && which != LBM_MOM_PRIM) return fail(LBM_E_INVAL, "bad moment set");
   if (dtype != LBM_DT_F32 && dtype != LBM_DT_F64) return fail(LBM_E_INVAL, "dtype must be F32 or F64");
@@ -563,6 +577,7 @@ lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells, int* block_threads,
                               float* ms_per_step, int* prefetch_tiles) {
   if (!b) return fail(LBM_E_INVAL, "batch is NULL");
+  LBM_ON_DEVICE(b->device);
   if (!b->initialized) return fail(LBM_E_STATE, "autotune needs an initialised batch");
   if (steps_per_trial < 2) steps_per_trial = 8;
   steps_per_trial += steps_per_trial & 1;  // whole pairs keep the parity

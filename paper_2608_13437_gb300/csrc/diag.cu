@@ -85,37 +85,80 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 }
 
 // Pass B: central differences of u (FP32, from the FP32 field), weighted by mu_local;
-// per-cell products in FP32, float-float sums.
+// per-cell products in FP32, float-float sums. Work items are columns of 32 x 8 cells
+// (x by y) over kZChunk planes; a persistent grid of kDiagBlocks blocks takes them
+// in a fixed order (block b: items b, b + grid, ...), so sums are reproducible. Each
+// thread marches up its (x, y) column: u at z - 1, z and z + 1 stays in registers, so
+// every value of the field is read from DRAM about once (plus one halo plane per
+// chunk); the x and y neighbours are loads of lines the block (or its neighbour
+// column, at about the same z) has just brought into L1 / L2.
+constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32;
+
 __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
                                                    const float* __restrict__ ufield,
                                                    double* __restrict__ partials) {
   FF acc[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   const long long n = P.ncell;
   const float inv_dx = (float)(1.0 / P.dx64), inv_2dx = (float)(0.5 / P.dx64);
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
-       cell += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(P, cell, x, y, z);
-    const CellIndex c = make_index(P, x, y, z);
-    float g[3][3];  // g[a][b] = d_a u_b
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      long long hi = c.nb[2 * a + 1], lo = c.nb[2 * a + 2];
-      float w = inv_2dx;
-      if (a == 0 && P.bc_x) {  // one-sided at a held end
-        hi = (x < P.nx - 1) ? c.nb[1] : c.own;
-        lo = (x > 0) ? c.nb[2] : c.own;
-        const int span = (x < P.nx - 1) + (x > 0);
-        w = span == 2 ? inv_2dx : (span == 1 ? inv_dx : 0.0f);
-      }
-#pragma unroll
-      for (int b = 0; b < 3; ++b) g[a][b] = mul(sub(ufield[b * n + hi], ufield[b * n + lo]), w);
+  const float* __restrict__ U0 = ufield;
+  const float* __restrict__ U1 = ufield + n;
+  const float* __restrict__ U2 = ufield + 2 * n;
+  const float* __restrict__ MU = ufield + 3 * n;
+  const int cols_x = (P.nx + kTileX - 1) / kTileX, cols_y = (P.ny + kTileY - 1) / kTileY;
+  const int chunks = (P.nz + kZChunk - 1) / kZChunk;
+  const long long items = (long long)cols_x * cols_y * chunks;
+  const long long nxy = (long long)P.nx * P.ny;
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cx = (int)(it % cols_x);
+    const long long r = it / cols_x;
+    const int cy = (int)(r % cols_y), cz = (int)(r / cols_y);
+    const int x = cx * kTileX + tx, y = cy * kTileY + ty;
+    if (x >= P.nx || y >= P.ny) continue;
+    // x neighbours (one-sided at held ends) and y neighbours (periodic)
+    int xh, xl;
+    float wxd = inv_2dx;
+    if (P.bc_x) {
+      xh = x < P.nx - 1 ? x + 1 : x;
+      xl = x > 0 ? x - 1 : x;
+      const int span = (x < P.nx - 1) + (x > 0);
+      wxd = span == 2 ? inv_2dx : (span == 1 ? inv_dx : 0.0f);
+    } else {
+      xh = x + 1 < P.nx ? x + 1 : 0;
+      xl = x > 0 ? x - 1 : P.nx - 1;
     }
-    const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
-    const float div = add(add(g[0][0], g[1][1]), g[2][2]);
-    const float mu_loc = ufield[3 * n + cell];
-    ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
-    ff_add(acc[1], mul(mu_loc, mul(div, div)));
+    const long long yh = (y + 1 < P.ny ? y + 1 : 0) * (long long)P.nx;
+    const long long yl = (y > 0 ? y - 1 : P.ny - 1) * (long long)P.nx;
+    const long long col = x + (long long)y * P.nx;  // cell of the column at z = 0
+    const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
+    const long long zlo = (z0 > 0 ? z0 - 1 : P.nz - 1) * nxy;
+    float pu0 = U0[zlo + col], pu1 = U1[zlo + col], pu2 = U2[zlo + col];
+    long long c = z0 * nxy + col;
+    float cu0 = U0[c], cu1 = U1[c], cu2 = U2[c];
+    for (int z = z0; z < z1; ++z, c += nxy) {
+      const long long cn = (z + 1 < P.nz ? c + nxy : col);
+      const float nu0 = U0[cn], nu1 = U1[cn], nu2 = U2[cn];
+      const long long plane = c - col;  // z * nx * ny
+      const long long ch = plane + y * (long long)P.nx + xh, cl = plane + y * (long long)P.nx + xl;
+      const long long cyh = plane + yh + x, cyl = plane + yl + x;
+      float g[3][3];  // g[a][b] = d_a u_b
+      g[0][0] = mul(sub(U0[ch], U0[cl]), wxd);
+      g[0][1] = mul(sub(U1[ch], U1[cl]), wxd);
+      g[0][2] = mul(sub(U2[ch], U2[cl]), wxd);
+      g[1][0] = mul(sub(U0[cyh], U0[cyl]), inv_2dx);
+      g[1][1] = mul(sub(U1[cyh], U1[cyl]), inv_2dx);
+      g[1][2] = mul(sub(U2[cyh], U2[cyl]), inv_2dx);
+      g[2][0] = mul(sub(nu0, pu0), inv_2dx);
+      g[2][1] = mul(sub(nu1, pu1), inv_2dx);
+      g[2][2] = mul(sub(nu2, pu2), inv_2dx);
+      const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
+      const float div = add(add(g[0][0], g[1][1]), g[2][2]);
+      const float mu_loc = MU[c];
+      ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
+      ff_add(acc[1], mul(mu_loc, mul(div, div)));
+      pu0 = cu0; pu1 = cu1; pu2 = cu2;
+      cu0 = nu0; cu1 = nu1; cu2 = nu2;
+    }
   }
   __shared__ FF sh[kBlock / 32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

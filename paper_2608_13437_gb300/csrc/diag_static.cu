@@ -15,9 +15,9 @@
 // domains of up to kStaticDiagMaxCells cells. It is part of the library image, so
 // it exists on every device that loads the library and stays until the process
 // exits. Host code cannot use the array's name as a device address, so the first
-// call on each device looks the address up with cudaGetSymbolAddress (with that
-// device current) and caches it; that first call should therefore come before any
-// stream capture. All calls share the array and the kernels write every element
+// call on each device looks the address up with cudaGetSymbolAddress (with the
+// handle's device made current) and caches it; that first call should therefore come
+// before any stream capture. A cached address does not survive cudaDeviceReset. All calls share the array and the kernels write every element
 // they later read within the same call, so no clearing is needed between calls;
 // two calls whose kernels overlap on the GPU (for instance from different streams
 // or threads) race on the array and must be serialised by the caller.
@@ -43,16 +43,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once).
-lbm_status scratch_address(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(LBM_E_CUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+// Device address of the scratch array on device `dev`, which the caller has made
+// current (looked up once per device).
+lbm_status scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(LBM_E_INVAL, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_addr[dev]) {
     void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_static_diag_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_diag_scratch);
     if (e != cudaSuccess || !ptr)
       return fail(LBM_E_CUDA, "cudaGetSymbolAddress of the diagnostic scratch failed: %s",
                   cudaGetErrorString(e));
@@ -68,14 +66,18 @@ lbm_status scratch_address(double** out) {
 using namespace lbm;
 
 extern "C" lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out) {
+  Range range_("lbm_diag_static");
   if (!h || !out) return fail(LBM_E_INVAL, "NULL argument");
   const HandleView v = handle_view(h);
   if (v.ncell > kStaticDiagMaxCells)
     return fail(LBM_E_INVAL,
                 "lbm_diag_static handles at most %lld cells (64^3); this domain has %lld cells "
                 "(use lbm_diag)", kStaticDiagMaxCells, v.ncell);
+  // the array and its address belong to the handle's device, whatever device the
+  // caller has current
+  LBM_ON_DEVICE(v.device);
   double* base = nullptr;
-  lbm_status s = scratch_address(&base);
+  lbm_status s = scratch_address(v.device, &base);
   if (s != LBM_OK) return s;
   float* ufield = reinterpret_cast<float*>(base);
   double* partials = base + kStaticU;
@@ -91,25 +93,5 @@ extern "C" lbm_status lbm_diag_static(lbm_handle* h, lbm_diag_t* out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, v.flag, sizeof(flag), cudaMemcpyDeviceToHost, v.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(v.stream);
   if (e != cudaSuccess) return fail(LBM_E_CUDA, "static diagnostics failed: %s", cudaGetErrorString(e));
-  const double n = (double)v.ncell;
-  out->step = (double)v.step;
-  out->time = (double)v.step * v.dt;
-  out->sum_rho = r[0];
-  out->sum_mx = r[1];
-  out->sum_my = r[2];
-  out->sum_mz = r[3];
-  out->sum_E = r[4];
-  out->ek_mean = r[5] / n;
-  out->nonfinite = r[6];
-  out->max_mach = r[9];
-  out->max_cfl = r[10];
-  out->min_rho = r[11];
-  out->min_T = r[12];
-  out->eps_s_raw = r[13] / n;
-  out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
-  latch_step_flag(h, flag);
-  if (r[6] > 0) latch_nonfinite(h);
-  if (stall_latched(h)) return fail(LBM_E_TIMEOUT, "a staged step gave up waiting for a bulk copy; re-init");
-  if (nonfinite_latched(h)) return fail(LBM_E_NONFINITE, "non-finite moments detected");
-  return LBM_OK;
+  return finish_diag(h, r, flag, v.step, out);
 }

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -72,17 +74,30 @@ inline long long step_diag_record_count(const DomainConst& P, int block_x) {
 }
 
 // Initial states (init.cu). kind: 0 TGV, 1 Riemann, 2 caller fields (rho, u, p),
-// 3 caller zeroth moments (14 fields).
+// 3 caller zeroth moments (14 fields). Host-computed FP32 constants; the device works
+// in FP32 only (the deviations from Q_ref are formed without cancellation).
 struct InitSpec {
   int kind;
-  double U0, M0, rho0;                 // TGV
-  int axis, split;                     // Riemann
-  double left[3], right[3];
-  const void* fields;                  // kind 2: [5][cell] rho, ux, uy, uz, p; kind 3: [14][cell] Q
+  // TGV (kind 0): U0, rho0 U0^2/16, 1/T0, p0, T0 and the differences between the FP64
+  // reference (rho0, p0/(gamma-1)) and its FP32 copy in DomainConst
+  const float* trig;                   // per axis: sin, cos, cos 2x of the nodes i dx
+  float U0, c_dp, inv_T0, p0, T0, drho_ref, dE_ref;
+  // Riemann (kind 1): deviations of (rho, rho u, E) and (rho, u, p), T of the two states
+  int axis, split;
+  float sD[2][5], sprim[2][5], sT[2];
+  // caller fields (kinds 2, 3): device (or mapped host) array, FP64 or FP32
+  const void* fields;
   int fields_f64;
-  double gamma, mu, kappa, tau_R, tau_q, inv_T_ref, c, dx;
-  int sutherland;
+  float inv_gm1_hi, inv_gm1_lo;        // 1/(gamma - 1) as a float-float pair
 };
+// Floats of the TGV table of a domain (3 per node of each axis).
+size_t tgv_table_floats(int nx, int ny, int nz);
+// Host set-up of the three kinds of initial state; P must hold the FP32 Q_ref already.
+void tgv_spec(const DomainConst& P, double gamma, double U0, double M0, double rho0, double dx,
+              InitSpec* sp, std::vector<float>* table);
+void riemann_spec(const DomainConst& P, double gamma, int axis, int split, const double left[3],
+                  const double right[3], InitSpec* sp);
+void fields_spec(double gamma, int kind, const void* fields, int f64, InitSpec* sp);
 // mode 0: per-field max |f - w Q_ref| into maxbits[14] (float bits); mode 1: write
 // the encoded populations (canonical slots) and the held-x ghost layers.
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,

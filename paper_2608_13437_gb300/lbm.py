@@ -43,7 +43,7 @@ class LbmInfo(ctypes.Structure):
         ("tau_q", ctypes.c_double), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
         ("scale", ctypes.c_double * 14), ("step", ctypes.c_longlong), ("ncell", ctypes.c_longlong),
         ("population_bytes", ctypes.c_size_t), ("store", ctypes.c_int), ("block_x", ctypes.c_int),
-        ("variant", ctypes.c_int), ("prefetch_tiles", ctypes.c_int),
+        ("variant", ctypes.c_int), ("prefetch_tiles", ctypes.c_int), ("device", ctypes.c_int),
     ]
 
 

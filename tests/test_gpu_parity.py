@@ -425,7 +425,8 @@ def test_staged_variants_need_whole_tile_rows(lbm):
     e = lbm.Domain(q, store="f16")
     e.init_tgv(1.0, 1.25, 1.0)
     t = e.autotune(pairs_per_trial=1)
-    assert t["candidates"] == 19  # 2 budgets x 2 blocks x 4 prefetch distances + 3 staged
+    # 2 budgets x 2 blocks x 4 prefetch distances; the staged forms are never candidates
+    assert t["candidates"] == 16 and t["variant"] in (0, 1)
     assert t["prefetch_tiles"] in (0, 512, 1024, 2048)
     assert e.info()["prefetch_tiles"] == t["prefetch_tiles"]
     e.close()
@@ -762,3 +763,79 @@ def test_error_paths(lbm):
     dom.step(2)
     dom.synchronize()
     dom.close()
+
+
+# --------------------------------------------------------------------------- initial states
+W_LAT = np.array([0.25] + [0.125] * 6)
+
+
+def _init_case(lbm, oracle_mod, case):
+    """A GPU domain (FP32 storage) and an oracle domain in the same initial state."""
+    if case.startswith("tgv"):
+        n = 32 if case == "tgv32" else 20
+        p = inputs.tgv_params(32)
+        p.update(nx=n, ny=n - 3 if n == 20 else n, nz=n - 7 if n == 20 else n, dx=2 * np.pi / n)
+        g, o = lbm.Domain(p), make_oracle(p)
+        g.init_tgv(1.0, 1.25, 1.0)
+        o.init_tgv(1.0, 1.25, 1.0)
+    elif case == "sod_held":
+        p = inputs.sod_params(64)
+        g, o = lbm.Domain(p), make_oracle(p)
+        g.init_riemann(0, 32, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+        o.init_riemann(0, 32, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    elif case.startswith("fields"):
+        # small perturbations of a uniform state: the deviations from Q_ref are about
+        # 1e-3 of the totals, where forming them as differences of FP32 totals would lose
+        # ten bits
+        p = inputs.tgv_params(16)
+        p.update(nx=37, ny=6, nz=5, dx=2 * np.pi / 37, sutherland=1)
+        s = inputs.random_smooth_state(37, 6, 5, seed=43, amp=1e-3)
+        g, o = lbm.Domain(p), make_oracle(p)
+        dt = np.float64 if case == "fields64" else np.float32
+        f = [np.asarray(s[k], dtype=dt).astype(np.float64) for k in ("rho", "ux", "uy", "uz", "p")]
+        g.init_fields(*f, dtype=dt)
+        o.init_fields(*f)
+    else:  # all 14 zeroth moments, with stress and heat flux
+        p = inputs.tgv_params(16)
+        p.update(nx=33, ny=4, nz=3, dx=2 * np.pi / 33, sutherland=1)
+        s = inputs.random_smooth_state(33, 4, 3, seed=47, amp=0.1)
+        rng = np.random.default_rng(48)
+        Q = np.zeros((NF, 3, 4, 33))
+        Q[0] = s["rho"]
+        for a, c in enumerate(("ux", "uy", "uz")):
+            Q[1 + a] = s["rho"] * s[c]
+        Q[4] = s["p"] / 0.4 + 0.5 * s["rho"] * (s["ux"] ** 2 + s["uy"] ** 2 + s["uz"] ** 2)
+        Q[5:] = 1e-3 * rng.standard_normal((9, 3, 4, 33))
+        g, o = lbm.Domain(p), make_oracle(p)
+        g.init_state(Q)
+        o.init_state(Q)
+    return g, o
+
+
+@pytest.mark.parametrize("case", ["tgv32", "tgv_ragged", "sod_held", "fields64", "fields32", "state"])
+def test_init_matches_oracle_equilibrium(lbm, oracle_mod, case):
+    """The initial populations, computed on the GPU in FP32 (deviations from Q_ref formed
+    analytically or as float-float differences; no FP64 arithmetic), against the FP64
+    oracle's equilibrium of the same state: per field, every population within 8 units
+    in the last place (FP32) of the field's largest deviation f - w_i Q_ref. The FP64
+    initial equilibrium this replaced was within half a unit of each value; 8 units
+    leave room for the FP32 products of the state and fluxes and stay 1/8 of the
+    precision the FP32 storage itself holds for the field."""
+    g, o = _init_case(lbm, oracle_mod, case)
+    info = g.info()
+    fg = g.populations()
+    fo = o.populations()
+    g.close()
+    Qref = np.zeros(NF)
+    Qref[0], Qref[4] = info["rho_ref"], info["E_ref"]
+    worst = 0.0
+    for k in range(NF):
+        dev = fo[k] - (W_LAT[:, None, None, None] * Qref[k])
+        S = np.abs(dev).max()
+        if S == 0:
+            assert np.array_equal(fg[k], fo[k]), k
+            continue
+        err = np.abs(fg[k] - fo[k]).max() / (S * 2.0 ** -24)
+        worst = max(worst, err)
+        assert err <= 8.0, (case, k, err)
+    print(f"{case}: largest error {worst:.2f} units of the field's largest deviation")

@@ -77,3 +77,28 @@ def test_static_diag_rejects_domains_above_its_limit(lbm):
     assert st == lbm.LBM_E_INVAL
     assert "at most 262144 cells" in lbm.lib().lbm_last_error().decode()
     dom.close()
+
+
+def test_static_diag_allocates_no_device_memory(lbm):
+    """The entry point's contract itself: on a fresh handle that lbm_diag has never
+    touched (so its O(cells) scratch does not exist), a call after a first one (which
+    may load the kernels and looks up the array's address) leaves the free device
+    memory unchanged, while lbm_diag's first call then takes its scratch."""
+    import torch
+    p = inputs.tgv_params(32)
+    p.update(nx=64, ny=64, nz=64)
+    dom = lbm.Domain(p)
+    dom.init_tgv(1.0, 1.25, 1.0)
+    dom.step(3)
+    first = _diag(lbm, "lbm_diag_static", dom)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    second = _diag(lbm, "lbm_diag_static", dom)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    assert second == first
+    _same(_diag(lbm, "lbm_diag", dom), second)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1  # lbm_diag allocated its 4 MB of scratch
+    dom.close()
