@@ -38,6 +38,16 @@ KERNEL_SOURCES = ("paper_2608_13437_gb300/csrc/lbm_device.cuh",
                   "paper_2608_13437_gb300/csrc/step_impl.cuh")
 
 
+def bench_config(n, store, world):
+    """The workload as both arms name it (the reference arm runs the oracle on a window
+    of this workload per step; its cpu_baseline says which)."""
+    ncell = n ** 3
+    return {"workload": workload_name(n), "n": n, "cells": ncell, "store": store,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "populations (%.1f GB) exceed the 129 MB L2; no flush between steps"
+                  % (BYTES_PER_CELL[store] / 2 * ncell / 1e9)}
+
+
 def workload_name(n):
     return (f"supersonic Taylor-Green vortex {n}^3 periodic [0,2pi)^3, gamma 1.4, Pr 0.71, M0 1.25, "
             "Re 1000, uniform T0, Sutherland, C_sigma 40, J_min 1e-2, omega_min 1.987, "
@@ -229,10 +239,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.n), "n": args.n, "store": "f64 (oracle)",
-                   "sample_per_step": f"{side}^3 window"},
+        "config": bench_config(args.n, args.store, world),
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
-                         "sample": f"FP64 oracle on a {side}^3 window of the {args.n}^3 TGV per step"},
+                         "sample": f"FP64 oracle (two-buffer pull streaming, FP64 arithmetic) on a "
+                                   f"{side}^3 window of the {args.n}^3 TGV per step"},
         "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -488,10 +498,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(n), "n": n, "cells": ncell, "store": args.store,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "populations (%.1f GB) exceed the 129 MB L2; no flush between steps"
-                             % (BYTES_PER_CELL[args.store] / 2 * ncell / 1e9)},
+            "config": bench_config(n, args.store, world),
             "roofline": roofline,
             "repeats": {"MLUPS": repeats, "best": max(repeats),
                         "median": sorted(repeats)[1], "steps": [args.steps, rep_steps, rep_steps]},
