@@ -318,9 +318,10 @@ def diag_costs(torch, dom, ms_step, reps=8):
         return a.elapsed_time(b) / reps
     sep = timed(dom.diag)
     fused = timed(lambda: dom.step_diag(1))
-    return {"plain_step_ms": round(ms_step, 4), "separate_diag_ms": round(sep, 4),
-            "step_with_diag_ms": round(fused, 4),
-            "in_step_extra_ms": round(fused - ms_step, 4)}
+    one = timed(lambda: dom.step(1))  # single plain steps, launched the same way
+    return {"plain_step_ms": round(ms_step, 4), "single_plain_step_ms": round(one, 4),
+            "separate_diag_ms": round(sep, 4), "step_with_diag_ms": round(fused, 4),
+            "in_step_extra_ms": round(fused - one, 4)}
 
 
 def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0):
@@ -527,6 +528,9 @@ def main():
     ap.add_argument("--only-batch", type=int, default=0, metavar="K",
                     help="run only the batched-mode leg on the first K seeded domains "
                          "(storage from --store)")
+    ap.add_argument("--only-diag", action="store_true",
+                    help="run only the diagnostics-cost leg (separate pass and in-step) on the "
+                         "--n^3 TGV with storage --store")
     ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -541,8 +545,21 @@ def main():
     build.build()
     world, rank, _ = dist_setup()
     args.cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and not args.only_batch:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.only_batch and not args.only_diag:
         args.cpu = cpu_baseline_subprocess(args.n)
+    if args.only_diag:
+        import torch
+
+        from paper_2608_13437_gb300 import inputs, lbm
+        torch.cuda.set_device(0)
+        dom = lbm.Domain(inputs.tgv_params(args.n), store=args.store)
+        dom.init_tgv(1.0, 1.25, 1.0)
+        ms, _ = time_steps(torch, dom, 20, args.warmup)
+        out = {"n": args.n, "store": args.store,
+               "diagnostics": diag_costs(torch, dom, ms / 20)}
+        dom.close()
+        print(json.dumps(out), flush=True)
+        return
     if args.only_batch:
         import torch
 

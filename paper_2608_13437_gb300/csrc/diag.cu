@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 // column, at about the same z) has just brought into L1 / L2.
 constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32;
 
-__global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
+__global__ void __launch_bounds__(kBlock, 4) k_diag_b(const DomainConst P,
                                                    const float* __restrict__ ufield,
                                                    double* __restrict__ partials) {
   FF acc[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -131,13 +131,26 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
     const long long yl = (y > 0 ? y - 1 : P.ny - 1) * (long long)P.nx;
     const long long col = x + (long long)y * P.nx;  // cell of the column at z = 0
     const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
+    // u at z - 1, z, z + 1 and mu_local at z in registers; the loads of u at z + 2 and
+    // of mu_local at z + 1 are issued one plane ahead, so two planes' DRAM reads are in
+    // flight per thread
     const long long zlo = (z0 > 0 ? z0 - 1 : P.nz - 1) * nxy;
-    float pu0 = U0[zlo + col], pu1 = U1[zlo + col], pu2 = U2[zlo + col];
     long long c = z0 * nxy + col;
+    const long long c1 = (z0 + 1 < P.nz ? c + nxy : col);
+    float pu0 = U0[zlo + col], pu1 = U1[zlo + col], pu2 = U2[zlo + col];
     float cu0 = U0[c], cu1 = U1[c], cu2 = U2[c];
+    float nu0 = U0[c1], nu1 = U1[c1], nu2 = U2[c1];
+    float mu_loc = MU[c];
     for (int z = z0; z < z1; ++z, c += nxy) {
-      const long long cn = (z + 1 < P.nz ? c + nxy : col);
-      const float nu0 = U0[cn], nu1 = U1[cn], nu2 = U2[cn];
+      const bool more = z + 1 < z1;
+      float qu0 = 0.0f, qu1 = 0.0f, qu2 = 0.0f, mu_n = 0.0f;
+      if (more) {
+        const long long c2 = (z + 2 < P.nz ? c + 2 * nxy : (z + 2 - P.nz) * nxy + col);
+        qu0 = U0[c2];
+        qu1 = U1[c2];
+        qu2 = U2[c2];
+        mu_n = MU[c + nxy];
+      }
       const long long plane = c - col;  // z * nx * ny
       const long long ch = plane + y * (long long)P.nx + xh, cl = plane + y * (long long)P.nx + xl;
       const long long cyh = plane + yh + x, cyl = plane + yl + x;
@@ -153,11 +166,12 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
       g[2][2] = mul(sub(nu2, pu2), inv_2dx);
       const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
       const float div = add(add(g[0][0], g[1][1]), g[2][2]);
-      const float mu_loc = MU[c];
       ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
       ff_add(acc[1], mul(mu_loc, mul(div, div)));
       pu0 = cu0; pu1 = cu1; pu2 = cu2;
       cu0 = nu0; cu1 = nu1; cu2 = nu2;
+      nu0 = qu0; nu1 = qu1; nu2 = qu2;
+      mu_loc = mu_n;
     }
   }
   __shared__ FF sh[kBlock / 32][2];
