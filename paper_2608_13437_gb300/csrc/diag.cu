@@ -86,24 +86,47 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 
 // Pass B: central differences of u (FP32, from the FP32 field), weighted by mu_local;
 // per-cell products in FP32, float-float sums. Work items are columns of 32 x 8 cells
-// (x by y) over kZChunk planes; a persistent grid of kDiagBlocks blocks takes them
-// in a fixed order (block b: items b, b + grid, ...), so sums are reproducible. Each
-// thread marches up its (x, y) column: u at z - 1, z and z + 1 stays in registers, so
-// every value of the field is read from DRAM about once (plus one halo plane per
-// chunk); the x and y neighbours are loads of lines the block (or its neighbour
-// column, at about the same z) has just brought into L1 / L2.
-constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32;
+// (x by y) over kZChunk planes; a persistent grid takes them in a fixed order (block b:
+// items b, b + grid, ...), so sums are reproducible. A block marches up its column
+// through a ring of kRing planes in shared memory: each plane holds u on the column
+// and a one-cell halo in x and y (wrapped periodically) and mu_local on the column,
+// filled by asynchronous copies (cp.async) issued kRing - 3 planes ahead of the plane
+// being differenced, so the DRAM reads of the planes ahead are in flight while the
+// block computes. Every value of the field is read from DRAM about once (the halo
+// comes from L2: neighbouring columns are processed at about the same z).
+constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32, kRing = 5;
+constexpr int kHaloX = kTileX + 2, kHaloY = kTileY + 2, kPlaneU = kHaloX * kHaloY;
+constexpr int kPlaneElems = 3 * kPlaneU + kTileX * kTileY;  // u (3 components) + mu_local
+constexpr int kCopiesPerThread = (kPlaneElems + kBlock - 1) / kBlock;
 
-__global__ void __launch_bounds__(kBlock, 4) k_diag_b(const DomainConst P,
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+struct DiagBPlanes {
+  float u[kRing][3][kPlaneU];
+  float mu[kRing][kTileX * kTileY];
+};
+
+__global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
                                                    const float* __restrict__ ufield,
                                                    double* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DiagBPlanes& sm = *reinterpret_cast<DiagBPlanes*>(smem_raw);
   FF acc[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   const long long n = P.ncell;
   const float inv_dx = (float)(1.0 / P.dx64), inv_2dx = (float)(0.5 / P.dx64);
-  const float* __restrict__ U0 = ufield;
-  const float* __restrict__ U1 = ufield + n;
-  const float* __restrict__ U2 = ufield + 2 * n;
-  const float* __restrict__ MU = ufield + 3 * n;
   const int cols_x = (P.nx + kTileX - 1) / kTileX, cols_y = (P.ny + kTileY - 1) / kTileY;
   const int chunks = (P.nz + kZChunk - 1) / kZChunk;
   const long long items = (long long)cols_x * cols_y * chunks;
@@ -113,66 +136,85 @@ __global__ void __launch_bounds__(kBlock, 4) k_diag_b(const DomainConst P,
     const int cx = (int)(it % cols_x);
     const long long r = it / cols_x;
     const int cy = (int)(r % cols_y), cz = (int)(r / cols_y);
-    const int x = cx * kTileX + tx, y = cy * kTileY + ty;
-    if (x >= P.nx || y >= P.ny) continue;
-    // x neighbours (one-sided at held ends) and y neighbours (periodic)
-    int xh, xl;
+    const int x0 = cx * kTileX, y0 = cy * kTileY;
+    const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
+    const int np = z1 - z0 + 2;  // planes z0 - 1 ... z1 (wrapped)
+    // in-plane offsets of this thread's copies (the same for every plane)
+    long long off[kCopiesPerThread];
+    float* dst[kCopiesPerThread];
+    int comp[kCopiesPerThread];
+#pragma unroll
+    for (int k = 0; k < kCopiesPerThread; ++k) {
+      const int e = threadIdx.x + k * kBlock;
+      comp[k] = -1;
+      if (e < 3 * kPlaneU) {
+        const int c = e / kPlaneU, j = e - c * kPlaneU;
+        const int ly = j / kHaloX, lx = j - ly * kHaloX;
+        const int gx = wrap_index(x0 - 1 + lx, P.nx), gy = wrap_index(y0 - 1 + ly, P.ny);
+        off[k] = (long long)c * n + (long long)gy * P.nx + gx;
+        comp[k] = c;
+        dst[k] = &sm.u[0][c][j];
+      } else if (e < kPlaneElems) {
+        const int j = e - 3 * kPlaneU;
+        const int ly = j / kTileX, lx = j - ly * kTileX;
+        const int gx = min(x0 + lx, P.nx - 1), gy = min(y0 + ly, P.ny - 1);
+        off[k] = 3 * n + (long long)gy * P.nx + gx;
+        comp[k] = 3;
+        dst[k] = &sm.mu[0][j];
+      }
+    }
+    // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRing
+    auto issue = [&](int p) {
+      if (p < np) {
+        const long long zoff = (long long)wrap_index(z0 - 1 + p, P.nz) * nxy;
+        const int slot = p % kRing;
+#pragma unroll
+        for (int k = 0; k < kCopiesPerThread; ++k) {
+          if (comp[k] < 0) continue;
+          const int stride = comp[k] < 3 ? 3 * kPlaneU : kTileX * kTileY;
+          cp_async4(dst[k] + slot * stride, ufield + off[k] + zoff);
+        }
+      }
+      cp_async_commit();  // an empty group past the last plane keeps the count uniform
+    };
+#pragma unroll
+    for (int p = 0; p < kRing - 1; ++p) issue(p);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool valid = x < P.nx && y < P.ny;
+    // x neighbours in the halo tile: one-sided at held ends (the own value)
+    const int hc = (ty + 1) * kHaloX + tx + 1;
+    int hxh = hc + 1, hxl = hc - 1;
     float wxd = inv_2dx;
     if (P.bc_x) {
-      xh = x < P.nx - 1 ? x + 1 : x;
-      xl = x > 0 ? x - 1 : x;
+      if (x == P.nx - 1) hxh = hc;
+      if (x == 0) hxl = hc;
       const int span = (x < P.nx - 1) + (x > 0);
       wxd = span == 2 ? inv_2dx : (span == 1 ? inv_dx : 0.0f);
-    } else {
-      xh = x + 1 < P.nx ? x + 1 : 0;
-      xl = x > 0 ? x - 1 : P.nx - 1;
     }
-    const long long yh = (y + 1 < P.ny ? y + 1 : 0) * (long long)P.nx;
-    const long long yl = (y > 0 ? y - 1 : P.ny - 1) * (long long)P.nx;
-    const long long col = x + (long long)y * P.nx;  // cell of the column at z = 0
-    const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
-    // u at z - 1, z, z + 1 and mu_local at z in registers; the loads of u at z + 2 and
-    // of mu_local at z + 1 are issued one plane ahead, so two planes' DRAM reads are in
-    // flight per thread
-    const long long zlo = (z0 > 0 ? z0 - 1 : P.nz - 1) * nxy;
-    long long c = z0 * nxy + col;
-    const long long c1 = (z0 + 1 < P.nz ? c + nxy : col);
-    float pu0 = U0[zlo + col], pu1 = U1[zlo + col], pu2 = U2[zlo + col];
-    float cu0 = U0[c], cu1 = U1[c], cu2 = U2[c];
-    float nu0 = U0[c1], nu1 = U1[c1], nu2 = U2[c1];
-    float mu_loc = MU[c];
-    for (int z = z0; z < z1; ++z, c += nxy) {
-      const bool more = z + 1 < z1;
-      float qu0 = 0.0f, qu1 = 0.0f, qu2 = 0.0f, mu_n = 0.0f;
-      if (more) {
-        const long long c2 = (z + 2 < P.nz ? c + 2 * nxy : (z + 2 - P.nz) * nxy + col);
-        qu0 = U0[c2];
-        qu1 = U1[c2];
-        qu2 = U2[c2];
-        mu_n = MU[c + nxy];
+    for (int i = 0; i < z1 - z0; ++i) {
+      issue(i + kRing - 1);
+      cp_async_wait<kRing - 3>();  // planes i, i + 1, i + 2 have landed
+      __syncthreads();
+      if (valid) {
+        const int sm_ = i % kRing, s0 = (i + 1) % kRing, sp = (i + 2) % kRing;
+        const float(*U)[kPlaneU] = sm.u[s0];
+        float g[3][3];  // g[a][b] = d_a u_b
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          g[0][b] = mul(sub(U[b][hxh], U[b][hxl]), wxd);
+          g[1][b] = mul(sub(U[b][hc + kHaloX], U[b][hc - kHaloX]), inv_2dx);
+          g[2][b] = mul(sub(sm.u[sp][b][hc], sm.u[sm_][b][hc]), inv_2dx);
+        }
+        const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
+        const float div = add(add(g[0][0], g[1][1]), g[2][2]);
+        const float mu_loc = sm.mu[s0][ty * kTileX + tx];
+        ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
+        ff_add(acc[1], mul(mu_loc, mul(div, div)));
       }
-      const long long plane = c - col;  // z * nx * ny
-      const long long ch = plane + y * (long long)P.nx + xh, cl = plane + y * (long long)P.nx + xl;
-      const long long cyh = plane + yh + x, cyl = plane + yl + x;
-      float g[3][3];  // g[a][b] = d_a u_b
-      g[0][0] = mul(sub(U0[ch], U0[cl]), wxd);
-      g[0][1] = mul(sub(U1[ch], U1[cl]), wxd);
-      g[0][2] = mul(sub(U2[ch], U2[cl]), wxd);
-      g[1][0] = mul(sub(U0[cyh], U0[cyl]), inv_2dx);
-      g[1][1] = mul(sub(U1[cyh], U1[cyl]), inv_2dx);
-      g[1][2] = mul(sub(U2[cyh], U2[cyl]), inv_2dx);
-      g[2][0] = mul(sub(nu0, pu0), inv_2dx);
-      g[2][1] = mul(sub(nu1, pu1), inv_2dx);
-      g[2][2] = mul(sub(nu2, pu2), inv_2dx);
-      const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
-      const float div = add(add(g[0][0], g[1][1]), g[2][2]);
-      ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
-      ff_add(acc[1], mul(mu_loc, mul(div, div)));
-      pu0 = cu0; pu1 = cu1; pu2 = cu2;
-      cu0 = nu0; cu1 = nu1; cu2 = nu2;
-      nu0 = qu0; nu1 = qu1; nu2 = qu2;
-      mu_loc = mu_n;
+      __syncthreads();  // slot i % kRing is refilled by the next iteration's copies
     }
+    cp_async_wait<0>();
+    __syncthreads();
   }
   __shared__ FF sh[kBlock / 32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,6 +235,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_diag_b(const DomainConst P,
     partials[(long long)blockIdx.x * 2 + threadIdx.x] = ff_value(r);
   }
 }
+
+constexpr size_t kDiagBSmem = sizeof(DiagBPlanes);
 
 // Fixed-order FP64 reduction of the block records of both passes (one block of
 // kBlock threads): thread t folds blocks t, t + kBlock, ... of every quantity, then a
@@ -270,7 +314,7 @@ cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void*
     case 1: launch_a_store<__half>(P, parity, pop, ghost, ufield, pa, s); break;
     default: launch_a_store<__nv_bfloat16>(P, parity, pop, ghost, ufield, pa, s); break;
   }
-  k_diag_b<<<kDiagBlocks, kBlock, 0, s>>>(P, ufield, pb);
+  k_diag_b<<<kDiagBlocks, kBlock, kDiagBSmem, s>>>(P, ufield, pb);
   k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, out16);
   return cudaGetLastError();
 }
@@ -281,7 +325,7 @@ cudaError_t launch_diag_records(const DomainConst& P, const float* rec, long lon
   double* pa = partials;
   double* pb = partials + (long long)kDiagBlocks * kDiagA;
   k_diag_records<<<kDiagBlocks, kBlock, 0, s>>>(rec, nrec, pa);
-  k_diag_b<<<kDiagBlocks, kBlock, 0, s>>>(P, ufield, pb);
+  k_diag_b<<<kDiagBlocks, kBlock, kDiagBSmem, s>>>(P, ufield, pb);
   k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, out16);
   return cudaGetLastError();
 }

@@ -104,11 +104,13 @@ def test_tgv_fp32_matches_fp64_oracle(lbm, oracle_mod, steps):
     _, chi, _ = o.sensor()
     assert (chi > 0).mean() > 0.01
     Qg, Qo = dom.moments(), o.moments()
-    # stress and heat flux: small fields, compared relative to their own norm
+    # stress and heat flux: small fields, compared relative to their own norm; observed
+    # on GB300 after 100 / 101 steps: tau 5.2e-6 / 7.2e-6, q 4.0e-5 / 3.6e-5 (the heat
+    # flux is the smaller field, so FP32 rounding weighs more in it); bounds about 3x
     e_tau, e_q = rel_l2(Qg[5:11], Qo[5:11]), rel_l2(Qg[11:14], Qo[11:14])
     print(f"TGV 32^3 after {steps} steps: tau rel-L2 {e_tau:.3e}, q rel-L2 {e_q:.3e}")
-    assert e_tau < 1e-3
-    assert e_q < 1e-3
+    assert e_tau < 2.5e-5
+    assert e_q < 1.2e-4
     dom.close()
 
 
