@@ -89,19 +89,35 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 // (x by y) over kZChunk planes; a persistent grid takes them in a fixed order (block b:
 // items b, b + grid, ...), so sums are reproducible. A block marches up its column
 // through a ring of kRing planes in shared memory: each plane holds u on the column
-// and a one-cell halo in x and y (wrapped periodically) and mu_local on the column,
-// filled by asynchronous copies (cp.async) issued kRing - 3 planes ahead of the plane
-// being differenced, so the DRAM reads of the planes ahead are in flight while the
-// block computes. Every value of the field is read from DRAM about once (the halo
-// comes from L2: neighbouring columns are processed at about the same z).
+// with a one-cell halo in x and y (wrapped periodically) and mu_local on the column,
+// filled by asynchronous copies (cp.async) two planes ahead of the plane being
+// differenced, so DRAM reads of the planes ahead are in flight while the block
+// computes. Full rows of 32 cells whose start is 16-byte aligned (nx a multiple of 4)
+// move as eight 16-byte copies; other tiles element by element. A thread keeps u of
+// its own cell at z - 1 and z in registers. Every value of the field is read from
+// DRAM about once (the halo comes from L2: neighbouring columns are processed at
+// about the same z).
 constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32, kRing = 5;
-constexpr int kHaloX = kTileX + 2, kHaloY = kTileY + 2, kPlaneU = kHaloX * kHaloY;
-constexpr int kPlaneElems = 3 * kPlaneU + kTileX * kTileY;  // u (3 components) + mu_local
-constexpr int kCopiesPerThread = (kPlaneElems + kBlock - 1) / kBlock;
+// a u row in shared memory: 3 pad, the x - 1 halo, 32 cells (16-byte aligned), the
+// x + 32 halo, 3 pad
+constexpr int kRowU = kTileX + 8, kRowsU = kTileY + 2, kPlaneU = kRowU * kRowsU;
+constexpr int kColX0 = 4;  // column of the first cell of the tile
+constexpr int kPlaneMu = kTileX * kTileY;
+// copies per plane: element-wise (34 x 10 u values x 3 + 32 x 8 mu values) and
+// vectorised (3 x 10 rows x 8 chunks + 3 x 10 x 2 halo values + 8 rows x 8 mu chunks)
+constexpr int kScalarCopies = 3 * (kTileX + 2) * kRowsU + kPlaneMu;
+constexpr int kVecU = 3 * kRowsU * (kTileX / 4), kVecHalo = 3 * kRowsU * 2,
+              kVecMu = kTileY * (kTileX / 4);
+constexpr int kVecCopies = kVecU + kVecHalo + kVecMu;
+constexpr int kMaxCopiesPerThread = (kScalarCopies + kBlock - 1) / kBlock;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -116,7 +132,16 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 
 struct DiagBPlanes {
   float u[kRing][3][kPlaneU];
-  float mu[kRing][kTileX * kTileY];
+  float mu[kRing][kPlaneMu];
+};
+
+// One copy of a plane: source offset within a z plane of the field (component
+// included), destination in ring slot 0, size (0: none, 4 or 16 bytes) and the ring
+// stride of its destination array.
+struct PlaneCopy {
+  long long off;
+  float* dst;
+  int bytes, stride;
 };
 
 __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
@@ -139,28 +164,50 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
     const int x0 = cx * kTileX, y0 = cy * kTileY;
     const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
     const int np = z1 - z0 + 2;  // planes z0 - 1 ... z1 (wrapped)
-    // in-plane offsets of this thread's copies (the same for every plane)
-    long long off[kCopiesPerThread];
-    float* dst[kCopiesPerThread];
-    int comp[kCopiesPerThread];
+    const bool vec = (P.nx % 4 == 0) && (x0 + kTileX <= P.nx);
+    // this thread's copies of every plane (the same offsets for each plane)
+    PlaneCopy cp[kMaxCopiesPerThread];
 #pragma unroll
-    for (int k = 0; k < kCopiesPerThread; ++k) {
-      const int e = threadIdx.x + k * kBlock;
-      comp[k] = -1;
-      if (e < 3 * kPlaneU) {
-        const int c = e / kPlaneU, j = e - c * kPlaneU;
-        const int ly = j / kHaloX, lx = j - ly * kHaloX;
-        const int gx = wrap_index(x0 - 1 + lx, P.nx), gy = wrap_index(y0 - 1 + ly, P.ny);
-        off[k] = (long long)c * n + (long long)gy * P.nx + gx;
-        comp[k] = c;
-        dst[k] = &sm.u[0][c][j];
-      } else if (e < kPlaneElems) {
-        const int j = e - 3 * kPlaneU;
-        const int ly = j / kTileX, lx = j - ly * kTileX;
-        const int gx = min(x0 + lx, P.nx - 1), gy = min(y0 + ly, P.ny - 1);
-        off[k] = 3 * n + (long long)gy * P.nx + gx;
-        comp[k] = 3;
-        dst[k] = &sm.mu[0][j];
+    for (int k = 0; k < kMaxCopiesPerThread; ++k) {
+      const int q = threadIdx.x + k * kBlock;
+      cp[k].bytes = 0;
+      cp[k].off = 0;
+      cp[k].dst = sm.mu[0];
+      cp[k].stride = 0;
+      if (vec) {
+        if (q < kVecU) {  // 16-byte chunk of a full u row
+          const int c = q / (kRowsU * 8), rem = q - c * (kRowsU * 8);
+          const int row = rem / 8, ch = rem - row * 8;
+          const int gy = wrap_index(y0 - 1 + row, P.ny);
+          cp[k] = {(long long)c * n + (long long)gy * P.nx + x0 + 4 * ch,
+                   &sm.u[0][c][row * kRowU + kColX0 + 4 * ch], 16, 3 * kPlaneU};
+        } else if (q < kVecU + kVecHalo) {  // the x halo of a u row
+          const int h = q - kVecU;
+          const int c = h / (kRowsU * 2), rem = h - c * (kRowsU * 2);
+          const int row = rem / 2, side = rem - row * 2;
+          const int gy = wrap_index(y0 - 1 + row, P.ny);
+          const int gx = side ? wrap_index(x0 + kTileX, P.nx) : wrap_index(x0 - 1, P.nx);
+          cp[k] = {(long long)c * n + (long long)gy * P.nx + gx,
+                   &sm.u[0][c][row * kRowU + (side ? kColX0 + kTileX : kColX0 - 1)], 4,
+                   3 * kPlaneU};
+        } else if (q < kVecCopies) {  // 16-byte chunk of a mu row
+          const int m = q - kVecU - kVecHalo;
+          const int row = m / 8, ch = m - row * 8;
+          const int gy = min(y0 + row, P.ny - 1);
+          cp[k] = {3 * n + (long long)gy * P.nx + x0 + 4 * ch, &sm.mu[0][row * kTileX + 4 * ch], 16,
+                   kPlaneMu};
+        }
+      } else if (q < 3 * (kTileX + 2) * kRowsU) {  // one u value of the halo tile
+        const int c = q / ((kTileX + 2) * kRowsU), j = q - c * ((kTileX + 2) * kRowsU);
+        const int row = j / (kTileX + 2), lx = j - row * (kTileX + 2);
+        const int gx = wrap_index(x0 - 1 + lx, P.nx), gy = wrap_index(y0 - 1 + row, P.ny);
+        cp[k] = {(long long)c * n + (long long)gy * P.nx + gx,
+                 &sm.u[0][c][row * kRowU + kColX0 - 1 + lx], 4, 3 * kPlaneU};
+      } else if (q < kScalarCopies) {  // one mu value of the tile
+        const int j = q - 3 * (kTileX + 2) * kRowsU;
+        const int row = j / kTileX, lx = j - row * kTileX;
+        const int gx = min(x0 + lx, P.nx - 1), gy = min(y0 + row, P.ny - 1);
+        cp[k] = {3 * n + (long long)gy * P.nx + gx, &sm.mu[0][j], 4, kPlaneMu};
       }
     }
     // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRing
@@ -169,10 +216,9 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
         const long long zoff = (long long)wrap_index(z0 - 1 + p, P.nz) * nxy;
         const int slot = p % kRing;
 #pragma unroll
-        for (int k = 0; k < kCopiesPerThread; ++k) {
-          if (comp[k] < 0) continue;
-          const int stride = comp[k] < 3 ? 3 * kPlaneU : kTileX * kTileY;
-          cp_async4(dst[k] + slot * stride, ufield + off[k] + zoff);
+        for (int k = 0; k < kMaxCopiesPerThread; ++k) {
+          if (cp[k].bytes == 16) cp_async16(cp[k].dst + slot * cp[k].stride, ufield + cp[k].off + zoff);
+          else if (cp[k].bytes == 4) cp_async4(cp[k].dst + slot * cp[k].stride, ufield + cp[k].off + zoff);
         }
       }
       cp_async_commit();  // an empty group past the last plane keeps the count uniform
@@ -182,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = x < P.nx && y < P.ny;
     // x neighbours in the halo tile: one-sided at held ends (the own value)
-    const int hc = (ty + 1) * kHaloX + tx + 1;
+    const int hc = (ty + 1) * kRowU + kColX0 + tx;
     int hxh = hc + 1, hxl = hc - 1;
     float wxd = inv_2dx;
     if (P.bc_x) {
@@ -191,19 +237,30 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
       const int span = (x < P.nx - 1) + (x > 0);
       wxd = span == 2 ? inv_2dx : (span == 1 ? inv_dx : 0.0f);
     }
+    float pu[3], cu[3];  // u of the own cell at z - 1 and z
     for (int i = 0; i < z1 - z0; ++i) {
-      issue(i + kRing - 1);
-      cp_async_wait<kRing - 3>();  // planes i, i + 1, i + 2 have landed
-      __syncthreads();
+      cp_async_wait<kRing - 4>();  // planes up to i + 2 have landed (this thread's copies)
+      __syncthreads();             // ... everyone's; and everyone is done with plane i - 1
+      issue(i + kRing - 1);        // into the slot of plane i - 1
+      const int s0 = (i + 1) % kRing, sp = (i + 2) % kRing;
+      if (i == 0) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          pu[b] = sm.u[0][b][hc];
+          cu[b] = sm.u[1 % kRing][b][hc];
+        }
+      }
       if (valid) {
-        const int sm_ = i % kRing, s0 = (i + 1) % kRing, sp = (i + 2) % kRing;
         const float(*U)[kPlaneU] = sm.u[s0];
         float g[3][3];  // g[a][b] = d_a u_b
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
+          const float nu = sm.u[sp][b][hc];
           g[0][b] = mul(sub(U[b][hxh], U[b][hxl]), wxd);
-          g[1][b] = mul(sub(U[b][hc + kHaloX], U[b][hc - kHaloX]), inv_2dx);
-          g[2][b] = mul(sub(sm.u[sp][b][hc], sm.u[sm_][b][hc]), inv_2dx);
+          g[1][b] = mul(sub(U[b][hc + kRowU], U[b][hc - kRowU]), inv_2dx);
+          g[2][b] = mul(sub(nu, pu[b]), inv_2dx);
+          pu[b] = cu[b];
+          cu[b] = nu;
         }
         const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
         const float div = add(add(g[0][0], g[1][1]), g[2][2]);
@@ -211,10 +268,9 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
         ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
         ff_add(acc[1], mul(mu_loc, mul(div, div)));
       }
-      __syncthreads();  // slot i % kRing is refilled by the next iteration's copies
     }
     cp_async_wait<0>();
-    __syncthreads();
+    __syncthreads();  // the next item refills every slot
   }
   __shared__ FF sh[kBlock / 32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
