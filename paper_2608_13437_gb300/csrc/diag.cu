@@ -85,31 +85,27 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 }
 
 // Pass B: central differences of u (FP32, from the FP32 field), weighted by mu_local;
-// per-cell products in FP32, float-float sums. Work items are columns of 32 x 8 cells
-// (x by y) over kZChunk planes; a persistent grid takes them in a fixed order (block b:
-// items b, b + grid, ...), so sums are reproducible. A block marches up its column
-// through a ring of kRing planes in shared memory: each plane holds u on the column
-// with a one-cell halo in x and y (wrapped periodically) and mu_local on the column,
-// filled by asynchronous copies (cp.async) two planes ahead of the plane being
-// differenced, so DRAM reads of the planes ahead are in flight while the block
-// computes. Full rows of 32 cells whose start is 16-byte aligned (nx a multiple of 4)
-// move as eight 16-byte copies; other tiles element by element. A thread keeps u of
-// its own cell at z - 1 and z in registers. Every value of the field is read from
-// DRAM about once (the halo comes from L2: neighbouring columns are processed at
-// about the same z).
-constexpr int kTileX = 32, kTileY = kBlock / 32, kZChunk = 32, kRing = 5;
-// a u row in shared memory: 3 pad, the x - 1 halo, 32 cells (16-byte aligned), the
-// x + 32 halo, 3 pad
-constexpr int kRowU = kTileX + 8, kRowsU = kTileY + 2, kPlaneU = kRowU * kRowsU;
-constexpr int kColX0 = 4;  // column of the first cell of the tile
-constexpr int kPlaneMu = kTileX * kTileY;
-// copies per plane: element-wise (34 x 10 u values x 3 + 32 x 8 mu values) and
-// vectorised (3 x 10 rows x 8 chunks + 3 x 10 x 2 halo values + 8 rows x 8 mu chunks)
-constexpr int kScalarCopies = 3 * (kTileX + 2) * kRowsU + kPlaneMu;
-constexpr int kVecU = 3 * kRowsU * (kTileX / 4), kVecHalo = 3 * kRowsU * 2,
-              kVecMu = kTileY * (kTileX / 4);
-constexpr int kVecCopies = kVecU + kVecHalo + kVecMu;
-constexpr int kMaxCopiesPerThread = (kScalarCopies + kBlock - 1) / kBlock;
+// per-cell products in FP32, float-float sums. Work items are columns of 32 x 16 cells
+// (x by y) over kZChunk planes; a grid of resident blocks takes them in a fixed order
+// (block b: items b, b + grid, ...), so sums are reproducible. A block of 128 threads
+// marches up its column; a thread owns 4 consecutive cells of one row. u of the
+// column with a one-cell halo in x and y (wrapped periodically) passes through a ring
+// of kRingB planes in shared memory, filled by asynchronous copies (cp.async) two
+// planes ahead of the plane being differenced (16-byte copies for full tile rows that
+// start 16-byte aligned, element copies otherwise), so the DRAM reads of the planes
+// ahead are in flight while the block computes. A thread keeps u of its own cells at
+// z - 1, z and z + 1 in registers and reads mu_local of its cells straight from the
+// field one plane ahead. The differences are taken unscaled and the products scaled
+// once by (1 / 2 dx)^2 (one-sided x differences at held ends carry a factor 2).
+// Every value of the field is read from DRAM about once (the halo comes from L2:
+// neighbouring columns are processed at about the same z).
+constexpr int kBlockB = 128, kTileX = 32, kTileY = 16, kCells = 4, kZChunk = 32, kRingB = 4;
+constexpr int kRowF = kTileX + 8;           // 3 pad, x - 1 halo, 32 cells, x + 32 halo, 3 pad
+constexpr int kRowsB = kTileY + 2;          // y - 1 halo, 16 rows, y + 16 halo
+constexpr int kColX0 = 4;                   // column of the tile's first cell (16-byte aligned)
+constexpr int kPlaneB = 3 * kRowsB * kRowF; // floats of one plane (three components)
+constexpr int kVecRows = 3 * kRowsB * (kTileX / 4), kVecHalo = 3 * kRowsB * 2;
+constexpr int kScalarCopies = 3 * kRowsB * (kTileX + 2);
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -130,33 +126,24 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-struct DiagBPlanes {
-  float u[kRing][3][kPlaneU];
-  float mu[kRing][kPlaneMu];
-};
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-// One copy of a plane: source offset within a z plane of the field (component
-// included), destination in ring slot 0, size (0: none, 4 or 16 bytes) and the ring
-// stride of its destination array.
-struct PlaneCopy {
-  long long off;
-  float* dst;
-  int bytes, stride;
-};
-
-__global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
-                                                   const float* __restrict__ ufield,
-                                                   double* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  DiagBPlanes& sm = *reinterpret_cast<DiagBPlanes*>(smem_raw);
+__global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
+                                                    const float* __restrict__ ufield,
+                                                    double* __restrict__ partials) {
+  extern __shared__ __align__(16) float ring[];  // [kRingB][3][kRowsB][kRowF]
+  __shared__ long long rowoff[kRowsB];           // (wrapped y) * nx of each tile row
+  __shared__ int halo_x[2];                      // wrapped x0 - 1 and x0 + 32
   FF acc[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   const long long n = P.ncell;
-  const float inv_dx = (float)(1.0 / P.dx64), inv_2dx = (float)(0.5 / P.dx64);
+  const float inv_2dx = (float)(0.5 / P.dx64);
+  const float s2 = mul(inv_2dx, inv_2dx);
   const int cols_x = (P.nx + kTileX - 1) / kTileX, cols_y = (P.ny + kTileY - 1) / kTileY;
   const int chunks = (P.nz + kZChunk - 1) / kZChunk;
   const long long items = (long long)cols_x * cols_y * chunks;
   const long long nxy = (long long)P.nx * P.ny;
-  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // cells 4 tx .. 4 tx + 3 of row ty
+  const float* MU = ufield + 3 * n;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const int cx = (int)(it % cols_x);
     const long long r = it / cols_x;
@@ -165,114 +152,134 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
     const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
     const int np = z1 - z0 + 2;  // planes z0 - 1 ... z1 (wrapped)
     const bool vec = (P.nx % 4 == 0) && (x0 + kTileX <= P.nx);
-    // this thread's copies of every plane (the same offsets for each plane)
-    PlaneCopy cp[kMaxCopiesPerThread];
-#pragma unroll
-    for (int k = 0; k < kMaxCopiesPerThread; ++k) {
-      const int q = threadIdx.x + k * kBlock;
-      cp[k].bytes = 0;
-      cp[k].off = 0;
-      cp[k].dst = sm.mu[0];
-      cp[k].stride = 0;
-      if (vec) {
-        if (q < kVecU) {  // 16-byte chunk of a full u row
-          const int c = q / (kRowsU * 8), rem = q - c * (kRowsU * 8);
-          const int row = rem / 8, ch = rem - row * 8;
-          const int gy = wrap_index(y0 - 1 + row, P.ny);
-          cp[k] = {(long long)c * n + (long long)gy * P.nx + x0 + 4 * ch,
-                   &sm.u[0][c][row * kRowU + kColX0 + 4 * ch], 16, 3 * kPlaneU};
-        } else if (q < kVecU + kVecHalo) {  // the x halo of a u row
-          const int h = q - kVecU;
-          const int c = h / (kRowsU * 2), rem = h - c * (kRowsU * 2);
-          const int row = rem / 2, side = rem - row * 2;
-          const int gy = wrap_index(y0 - 1 + row, P.ny);
-          const int gx = side ? wrap_index(x0 + kTileX, P.nx) : wrap_index(x0 - 1, P.nx);
-          cp[k] = {(long long)c * n + (long long)gy * P.nx + gx,
-                   &sm.u[0][c][row * kRowU + (side ? kColX0 + kTileX : kColX0 - 1)], 4,
-                   3 * kPlaneU};
-        } else if (q < kVecCopies) {  // 16-byte chunk of a mu row
-          const int m = q - kVecU - kVecHalo;
-          const int row = m / 8, ch = m - row * 8;
-          const int gy = min(y0 + row, P.ny - 1);
-          cp[k] = {3 * n + (long long)gy * P.nx + x0 + 4 * ch, &sm.mu[0][row * kTileX + 4 * ch], 16,
-                   kPlaneMu};
-        }
-      } else if (q < 3 * (kTileX + 2) * kRowsU) {  // one u value of the halo tile
-        const int c = q / ((kTileX + 2) * kRowsU), j = q - c * ((kTileX + 2) * kRowsU);
-        const int row = j / (kTileX + 2), lx = j - row * (kTileX + 2);
-        const int gx = wrap_index(x0 - 1 + lx, P.nx), gy = wrap_index(y0 - 1 + row, P.ny);
-        cp[k] = {(long long)c * n + (long long)gy * P.nx + gx,
-                 &sm.u[0][c][row * kRowU + kColX0 - 1 + lx], 4, 3 * kPlaneU};
-      } else if (q < kScalarCopies) {  // one mu value of the tile
-        const int j = q - 3 * (kTileX + 2) * kRowsU;
-        const int row = j / kTileX, lx = j - row * kTileX;
-        const int gx = min(x0 + lx, P.nx - 1), gy = min(y0 + row, P.ny - 1);
-        cp[k] = {3 * n + (long long)gy * P.nx + gx, &sm.mu[0][j], 4, kPlaneMu};
-      }
-    }
-    // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRing
+    if (threadIdx.x < kRowsB) rowoff[threadIdx.x] = (long long)wrap_index(y0 - 1 + threadIdx.x, P.ny) * P.nx;
+    if (threadIdx.x == kRowsB) halo_x[0] = wrap_index(x0 - 1, P.nx);
+    if (threadIdx.x == kRowsB + 1) halo_x[1] = wrap_index(x0 + kTileX, P.nx);
+    __syncthreads();
+    // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRingB
     auto issue = [&](int p) {
       if (p < np) {
         const long long zoff = (long long)wrap_index(z0 - 1 + p, P.nz) * nxy;
-        const int slot = p % kRing;
-#pragma unroll
-        for (int k = 0; k < kMaxCopiesPerThread; ++k) {
-          if (cp[k].bytes == 16) cp_async16(cp[k].dst + slot * cp[k].stride, ufield + cp[k].off + zoff);
-          else if (cp[k].bytes == 4) cp_async4(cp[k].dst + slot * cp[k].stride, ufield + cp[k].off + zoff);
+        float* slot = ring + (p % kRingB) * kPlaneB;
+        if (vec) {
+          for (int q = threadIdx.x; q < kVecRows + kVecHalo; q += kBlockB) {
+            if (q < kVecRows) {  // 16-byte chunk of a full row
+              const int c = q / (kRowsB * 8), rem = q - c * (kRowsB * 8);
+              const int row = rem >> 3, ch = rem & 7;
+              cp_async16(slot + (c * kRowsB + row) * kRowF + kColX0 + 4 * ch,
+                         ufield + c * n + zoff + rowoff[row] + x0 + 4 * ch);
+            } else {  // the x halo of a row
+              const int h = q - kVecRows;
+              const int c = h / (kRowsB * 2), rem = h - c * (kRowsB * 2);
+              const int row = rem >> 1, side = rem & 1;
+              cp_async4(slot + (c * kRowsB + row) * kRowF + (side ? kColX0 + kTileX : kColX0 - 1),
+                        ufield + c * n + zoff + rowoff[row] + halo_x[side]);
+            }
+          }
+        } else {
+          for (int q = threadIdx.x; q < kScalarCopies; q += kBlockB) {
+            const int c = q / (kRowsB * (kTileX + 2)), rem = q - c * (kRowsB * (kTileX + 2));
+            const int row = rem / (kTileX + 2), lx = rem - row * (kTileX + 2);
+            cp_async4(slot + (c * kRowsB + row) * kRowF + kColX0 - 1 + lx,
+                      ufield + c * n + zoff + rowoff[row] + wrap_index(x0 - 1 + lx, P.nx));
+          }
         }
       }
       cp_async_commit();  // an empty group past the last plane keeps the count uniform
     };
 #pragma unroll
-    for (int p = 0; p < kRing - 1; ++p) issue(p);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool valid = x < P.nx && y < P.ny;
-    // x neighbours in the halo tile: one-sided at held ends (the own value)
-    const int hc = (ty + 1) * kRowU + kColX0 + tx;
-    int hxh = hc + 1, hxl = hc - 1;
-    float wxd = inv_2dx;
-    if (P.bc_x) {
-      if (x == P.nx - 1) hxh = hc;
-      if (x == 0) hxl = hc;
+    for (int p = 0; p < kRingB; ++p) issue(p);
+    const int xa = x0 + kCells * tx, y = y0 + ty;
+    const bool row_ok = y < P.ny;
+    int nvalid = row_ok ? min(kCells, P.nx - xa) : 0;
+    if (nvalid < 0) nvalid = 0;
+    // mu_local of the own cells at plane z (direct loads, one plane ahead)
+    const long long own = (long long)y * P.nx + xa;
+    auto load_mu = [&](int z, float (&m)[kCells]) {
+      const long long o = (long long)z * nxy + own;
+      if (vec && row_ok) {
+        const float4 v = *reinterpret_cast<const float4*>(MU + o);
+        m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < kCells; ++j) m[j] = j < nvalid ? MU[o + j] : 0.0f;
+      }
+    };
+    // one-sided x differences at held ends: factor 2 on the one available difference
+    float fx[kCells];
+    bool own_l[kCells], own_r[kCells];
+#pragma unroll
+    for (int j = 0; j < kCells; ++j) {
+      const int x = xa + j;
+      own_l[j] = P.bc_x && x == 0;
+      own_r[j] = P.bc_x && x == P.nx - 1;
       const int span = (x < P.nx - 1) + (x > 0);
-      wxd = span == 2 ? inv_2dx : (span == 1 ? inv_dx : 0.0f);
+      fx[j] = !P.bc_x ? 1.0f : (span == 2 ? 1.0f : (span == 1 ? 2.0f : 0.0f));
     }
-    float pu[3], cu[3];  // u of the own cell at z - 1 and z
+    const int hc = (ty + 1) * kRowF + kColX0 + kCells * tx;  // own first cell in a plane
+    float pu[3][kCells], cu[3][kCells], mu[kCells], mu_n[kCells];
+    cp_async_wait<kRingB - 2>();  // planes 0 and 1
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 a = lds4(ring + 0 * kPlaneB + c * kRowsB * kRowF + hc);
+      const float4 b = lds4(ring + 1 * kPlaneB + c * kRowsB * kRowF + hc);
+      pu[c][0] = a.x; pu[c][1] = a.y; pu[c][2] = a.z; pu[c][3] = a.w;
+      cu[c][0] = b.x; cu[c][1] = b.y; cu[c][2] = b.z; cu[c][3] = b.w;
+    }
+    load_mu(z0, mu);
     for (int i = 0; i < z1 - z0; ++i) {
-      cp_async_wait<kRing - 4>();  // planes up to i + 2 have landed (this thread's copies)
-      __syncthreads();             // ... everyone's; and everyone is done with plane i - 1
-      issue(i + kRing - 1);        // into the slot of plane i - 1
-      const int s0 = (i + 1) % kRing, sp = (i + 2) % kRing;
-      if (i == 0) {
+      cp_async_wait<kRingB - 3>();  // planes up to i + 2 have landed (this thread's copies)
+      __syncthreads();              // ... everyone's; and everyone is done with plane i
+      issue(i + kRingB);            // into the slot of plane i
+      if (i + 1 < z1 - z0) load_mu(z0 + i + 1, mu_n);
+      const float* S0 = ring + ((i + 1) % kRingB) * kPlaneB;  // plane z
+      const float* SP = ring + ((i + 2) % kRingB) * kPlaneB;  // plane z + 1
+      float d[3][3][kCells];  // d[a][b][j]: unscaled central difference of u_b along a
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          pu[b] = sm.u[0][b][hc];
-          cu[b] = sm.u[1 % kRing][b][hc];
+      for (int c = 0; c < 3; ++c) {
+        const float* C0 = S0 + c * kRowsB * kRowF + hc;
+        const float4 nu = lds4(SP + c * kRowsB * kRowF + hc);
+        const float4 ym = lds4(C0 - kRowF), yp = lds4(C0 + kRowF);
+        const float xl = C0[-1], xr = C0[kCells];
+        const float nv[kCells] = {nu.x, nu.y, nu.z, nu.w};
+        const float ymv[kCells] = {ym.x, ym.y, ym.z, ym.w}, ypv[kCells] = {yp.x, yp.y, yp.z, yp.w};
+#pragma unroll
+        for (int j = 0; j < kCells; ++j) {
+          float right = j + 1 < kCells ? cu[c][j + 1] : xr;
+          float left = j > 0 ? cu[c][j - 1] : xl;
+          if (own_r[j]) right = cu[c][j];
+          if (own_l[j]) left = cu[c][j];
+          d[0][c][j] = mul(sub(right, left), fx[j]);
+          d[1][c][j] = sub(ypv[j], ymv[j]);
+          d[2][c][j] = sub(nv[j], pu[c][j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kCells; ++j) {  // march: z becomes z - 1, z + 1 becomes z
+          pu[c][j] = cu[c][j];
+          cu[c][j] = nv[j];
         }
       }
-      if (valid) {
-        const float(*U)[kPlaneU] = sm.u[s0];
-        float g[3][3];  // g[a][b] = d_a u_b
+      float ss = 0.0f, sd = 0.0f;
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const float nu = sm.u[sp][b][hc];
-          g[0][b] = mul(sub(U[b][hxh], U[b][hxl]), wxd);
-          g[1][b] = mul(sub(U[b][hc + kRowU], U[b][hc - kRowU]), inv_2dx);
-          g[2][b] = mul(sub(nu, pu[b]), inv_2dx);
-          pu[b] = cu[b];
-          cu[b] = nu;
+      for (int j = 0; j < kCells; ++j) {
+        if (j < nvalid) {
+          const float wx = sub(d[1][2][j], d[2][1][j]), wy = sub(d[2][0][j], d[0][2][j]),
+                      wz = sub(d[0][1][j], d[1][0][j]);
+          const float div = add(add(d[0][0][j], d[1][1][j]), d[2][2][j]);
+          ss = fma_(mu[j], fma_(wz, wz, fma_(wy, wy, mul(wx, wx))), ss);
+          sd = fma_(mu[j], mul(div, div), sd);
         }
-        const float wx = sub(g[1][2], g[2][1]), wy = sub(g[2][0], g[0][2]), wz = sub(g[0][1], g[1][0]);
-        const float div = add(add(g[0][0], g[1][1]), g[2][2]);
-        const float mu_loc = sm.mu[s0][ty * kTileX + tx];
-        ff_add(acc[0], mul(mu_loc, fma_(wz, wz, fma_(wy, wy, mul(wx, wx)))));
-        ff_add(acc[1], mul(mu_loc, mul(div, div)));
       }
+      ff_add(acc[0], mul(ss, s2));
+      ff_add(acc[1], mul(sd, s2));
+#pragma unroll
+      for (int j = 0; j < kCells; ++j) mu[j] = mu_n[j];
     }
     cp_async_wait<0>();
-    __syncthreads();  // the next item refills every slot
+    __syncthreads();  // the next item refills every slot and the row table
   }
-  __shared__ FF sh[kBlock / 32][2];
+  __shared__ FF sh[kBlockB / 32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -287,21 +294,37 @@ __global__ void __launch_bounds__(kBlock) k_diag_b(const DomainConst P,
   __syncthreads();
   if (threadIdx.x < 2) {
     FF r = sh[0][threadIdx.x];
-    for (int w = 1; w < kBlock / 32; ++w) ff_merge(r, sh[w][threadIdx.x]);
+    for (int w = 1; w < kBlockB / 32; ++w) ff_merge(r, sh[w][threadIdx.x]);
     partials[(long long)blockIdx.x * 2 + threadIdx.x] = ff_value(r);
   }
 }
 
-constexpr size_t kDiagBSmem = sizeof(DiagBPlanes);
+constexpr size_t kDiagBSmem = sizeof(float) * kRingB * kPlaneB;
 
-// Fixed-order FP64 reduction of the block records of both passes (one block of
-// kBlock threads): thread t folds blocks t, t + kBlock, ... of every quantity, then a
+// Grid of pass B: the blocks resident on the device at once (one wave), at most
+// kDiagBlocks (the partials buffer holds that many).
+int diag_b_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_b, kBlockB, kDiagBSmem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return kDiagBlocks;
+  }
+  const int g = sms * per_sm;
+  return g < 1 ? 1 : (g > kDiagBlocks ? kDiagBlocks : g);
+}
+
+// Fixed-order FP64 reduction of the block records of both passes (nblocks records of
+// pass A or R, nblocks_b <= nblocks of pass B; one block of kBlock threads): thread t
+// folds blocks t, t + kBlock, ... of every quantity, then a
 // shared-memory tree combines the threads in a fixed pattern. The reference density
 // and energy are added back once per cell at the end.
 __global__ void __launch_bounds__(kBlock) k_diag_final(const DomainConst P,
                                                        const double* __restrict__ pa,
                                                        const double* __restrict__ pb, int nblocks,
-                                                       double* __restrict__ out) {
+                                                       int nblocks_b, double* __restrict__ out) {
   constexpr int kN = kDiagA + 2;
   __shared__ double sh[kN][kBlock];
   const int t = threadIdx.x;
@@ -314,8 +337,10 @@ __global__ void __launch_bounds__(kBlock) k_diag_final(const DomainConst P,
       const double v = pa[(long long)b * kDiagA + j];
       r[j] = j < 9 ? r[j] + v : (j < 11 ? fmax(r[j], v) : fmin(r[j], v));
     }
-    r[kDiagA] += pb[(long long)b * 2];
-    r[kDiagA + 1] += pb[(long long)b * 2 + 1];
+    if (b < nblocks_b) {
+      r[kDiagA] += pb[(long long)b * 2];
+      r[kDiagA + 1] += pb[(long long)b * 2 + 1];
+    }
   }
 #pragma unroll
   for (int j = 0; j < kN; ++j) sh[j][t] = r[j];
@@ -370,8 +395,9 @@ cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void*
     case 1: launch_a_store<__half>(P, parity, pop, ghost, ufield, pa, s); break;
     default: launch_a_store<__nv_bfloat16>(P, parity, pop, ghost, ufield, pa, s); break;
   }
-  k_diag_b<<<kDiagBlocks, kBlock, kDiagBSmem, s>>>(P, ufield, pb);
-  k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, out16);
+  const int gb = diag_b_grid();
+  k_diag_b<<<gb, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+  k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, gb, out16);
   return cudaGetLastError();
 }
 
@@ -381,8 +407,9 @@ cudaError_t launch_diag_records(const DomainConst& P, const float* rec, long lon
   double* pa = partials;
   double* pb = partials + (long long)kDiagBlocks * kDiagA;
   k_diag_records<<<kDiagBlocks, kBlock, 0, s>>>(rec, nrec, pa);
-  k_diag_b<<<kDiagBlocks, kBlock, kDiagBSmem, s>>>(P, ufield, pb);
-  k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, out16);
+  const int gb = diag_b_grid();
+  k_diag_b<<<gb, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+  k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, gb, out16);
   return cudaGetLastError();
 }
 
