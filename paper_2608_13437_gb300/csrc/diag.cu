@@ -87,33 +87,35 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 // Pass B: central differences of u (FP32, from the FP32 field), weighted by mu_local;
 // per-cell products in FP32, float-float sums. Work items are columns of 32 x 16 cells
 // (x by y) over kZChunk planes; a grid of resident blocks takes them in a fixed order
-// (block b: items b, b + grid, ...), so sums are reproducible. A block of 128 threads
-// marches up its column; a thread owns 4 consecutive cells of one row. u of the
-// column with a one-cell halo in x and y (wrapped periodically) passes through a ring
-// of kRingB planes in shared memory, filled by asynchronous copies (cp.async) two
-// planes ahead of the plane being differenced (16-byte copies for full tile rows that
-// start 16-byte aligned, element copies otherwise), so the DRAM reads of the planes
-// ahead are in flight while the block computes. A thread keeps u of its own cells at
-// z - 1, z and z + 1 in registers and reads mu_local of its cells straight from the
-// field one plane ahead. The differences are taken unscaled and the products scaled
-// once by (1 / 2 dx)^2 (one-sided x differences at held ends carry a factor 2).
-// Every value of the field is read from DRAM about once (the halo comes from L2:
-// neighbouring columns are processed at about the same z).
-constexpr int kBlockB = 128, kTileX = 32, kTileY = 16, kCells = 4, kZChunk = 32, kRingB = 4;
+// (block b: items b, b + grid, ...), so sums are reproducible. A block of 256 threads
+// marches up its column; a thread owns 2 consecutive cells of one row. u of the column
+// with a one-cell halo in x and y (wrapped periodically), and mu_local of the column,
+// pass through a ring of kRingB planes in shared memory, filled by asynchronous copies
+// (cp.async) two planes ahead of the plane being differenced, so the DRAM reads of the
+// planes ahead are in flight while the block computes. When nx is a multiple of 32
+// every tile row is a full, 16-byte aligned row and moves as 16-byte copies whose
+// addresses a thread fixes once per item; otherwise element copies (a separate
+// instantiation). A thread keeps u of its own cells at z - 1, z and z + 1 in three
+// register sets whose roles rotate. The differences are taken unscaled and the
+// products scaled once by (1 / 2 dx)^2 (one-sided x differences at held ends carry a
+// factor 2); the products of two planes are summed in FP32 before each float-float
+// addition. Every value of the field is read from DRAM about once (the halo comes
+// from L2: neighbouring columns are processed at about the same z).
+constexpr int kCells = 2;  // consecutive cells of a row per thread
+constexpr int kTileX = 32, kTileY = 16, kZChunk = 32, kRingB = 4;
+constexpr int kThreadsX = kTileX / kCells, kBlockB = kThreadsX * kTileY;
 constexpr int kRowF = kTileX + 8;           // 3 pad, x - 1 halo, 32 cells, x + 32 halo, 3 pad
 constexpr int kRowsB = kTileY + 2;          // y - 1 halo, 16 rows, y + 16 halo
 constexpr int kColX0 = 4;                   // column of the tile's first cell (16-byte aligned)
-constexpr int kPlaneB = 3 * kRowsB * kRowF; // floats of one plane (three components)
+constexpr int kPlaneU = 3 * kRowsB * kRowF; // floats of u on one plane (three components)
+constexpr int kPlaneB = kPlaneU + kTileX * kTileY;  // ... followed by mu_local of the tile
 constexpr int kVecRows = 3 * kRowsB * (kTileX / 4), kVecHalo = 3 * kRowsB * 2;
-constexpr int kScalarCopies = 3 * kRowsB * (kTileX + 2);
+constexpr int kVecMu = kTileY * (kTileX / 4);
+constexpr int kScalarCopies = 3 * kRowsB * (kTileX + 2) + kTileX * kTileY;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -126,9 +128,21 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// kCells consecutive floats from a kCells * 4-byte aligned address
+__device__ __forceinline__ void ldv(const float* p, float (&o)[kCells]) {
+  if constexpr (kCells == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+}
 
-__global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
+// kVec: nx is a multiple of 32, so every tile row is a full, 16-byte aligned row of 32
+// cells (vector copies and loads); otherwise element copies with wrapped x.
+template <bool kVec>
+__global__ void __launch_bounds__(kBlockB, 4) k_diag_b(const DomainConst P,
                                                     const float* __restrict__ ufield,
                                                     double* __restrict__ partials) {
   extern __shared__ __align__(16) float ring[];  // [kRingB][3][kRowsB][kRowF]
@@ -142,8 +156,7 @@ __global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
   const int chunks = (P.nz + kZChunk - 1) / kZChunk;
   const long long items = (long long)cols_x * cols_y * chunks;
   const long long nxy = (long long)P.nx * P.ny;
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // cells 4 tx .. 4 tx + 3 of row ty
-  const float* MU = ufield + 3 * n;
+  const int tx = threadIdx.x % kThreadsX, ty = threadIdx.x / kThreadsX;  // cells kCells tx... of row ty
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const int cx = (int)(it % cols_x);
     const long long r = it / cols_x;
@@ -151,39 +164,86 @@ __global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
     const int x0 = cx * kTileX, y0 = cy * kTileY;
     const int z0 = cz * kZChunk, z1 = min(z0 + kZChunk, P.nz);
     const int np = z1 - z0 + 2;  // planes z0 - 1 ... z1 (wrapped)
-    const bool vec = (P.nx % 4 == 0) && (x0 + kTileX <= P.nx);
+    constexpr bool vec = kVec;
     if (threadIdx.x < kRowsB) rowoff[threadIdx.x] = (long long)wrap_index(y0 - 1 + threadIdx.x, P.ny) * P.nx;
     if (threadIdx.x == kRowsB) halo_x[0] = wrap_index(x0 - 1, P.nx);
     if (threadIdx.x == kRowsB + 1) halo_x[1] = wrap_index(x0 + kTileX, P.nx);
     __syncthreads();
-    // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRingB
+    // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRingB.
+    // Full rows: this thread's (at most 3) copies of every plane, fixed per item: copy 0
+    // a 16-byte u row chunk, copy 1 a u row chunk or an x-halo value, copy 2 an x-halo
+    // value, a 16-byte mu row chunk or none (432 + 108 + 128 = 668 copies over 256
+    // threads).
+    static_assert(kBlockB == 256 && kVecRows == 432 && kVecHalo == 108 && kVecMu == 128,
+                  "copy split");
+    const float* csrc[3] = {ufield, ufield, ufield};
+    unsigned cdst[3] = {0u, 0u, 0u};
+    if constexpr (vec) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int q = threadIdx.x + k * kBlockB;
+        if (q < kVecRows) {
+          const int c = q / (kRowsB * 8), rem = q - c * (kRowsB * 8);
+          const int row = rem >> 3, ch = rem & 7;
+          csrc[k] = ufield + c * n + rowoff[row] + x0 + 4 * ch;
+          cdst[k] = (unsigned)__cvta_generic_to_shared(ring + (c * kRowsB + row) * kRowF + kColX0 + 4 * ch);
+        } else if (q < kVecRows + kVecHalo) {
+          const int h = q - kVecRows;
+          const int c = h / (kRowsB * 2), rem = h - c * (kRowsB * 2);
+          const int row = rem >> 1, side = rem & 1;
+          csrc[k] = ufield + c * n + rowoff[row] + halo_x[side];
+          cdst[k] = (unsigned)__cvta_generic_to_shared(
+              ring + (c * kRowsB + row) * kRowF + (side ? kColX0 + kTileX : kColX0 - 1));
+        } else if (q < kVecRows + kVecHalo + kVecMu) {  // mu_local rows (no halo)
+          const int m = q - kVecRows - kVecHalo;
+          const int row = m >> 3, ch = m & 7;
+          const int gy = min(y0 + row, P.ny - 1);
+          csrc[k] = ufield + 3 * n + (long long)gy * P.nx + x0 + 4 * ch;
+          cdst[k] = (unsigned)__cvta_generic_to_shared(ring + kPlaneU + row * kTileX + 4 * ch);
+        }
+      }
+    }
+    const bool c1_is_row = threadIdx.x + kBlockB < kVecRows;
+    const int q2 = threadIdx.x + 2 * kBlockB;
+    const bool c2_is_halo = q2 < kVecRows + kVecHalo;
+    const bool c2_is_mu = !c2_is_halo && q2 < kVecRows + kVecHalo + kVecMu;
+    long long zoff = (long long)wrap_index(z0 - 1, P.nz) * nxy;  // of the next plane to issue
     auto issue = [&](int p) {
       if (p < np) {
-        const long long zoff = (long long)wrap_index(z0 - 1 + p, P.nz) * nxy;
-        float* slot = ring + (p % kRingB) * kPlaneB;
-        if (vec) {
-          for (int q = threadIdx.x; q < kVecRows + kVecHalo; q += kBlockB) {
-            if (q < kVecRows) {  // 16-byte chunk of a full row
-              const int c = q / (kRowsB * 8), rem = q - c * (kRowsB * 8);
-              const int row = rem >> 3, ch = rem & 7;
-              cp_async16(slot + (c * kRowsB + row) * kRowF + kColX0 + 4 * ch,
-                         ufield + c * n + zoff + rowoff[row] + x0 + 4 * ch);
-            } else {  // the x halo of a row
-              const int h = q - kVecRows;
-              const int c = h / (kRowsB * 2), rem = h - c * (kRowsB * 2);
-              const int row = rem >> 1, side = rem & 1;
-              cp_async4(slot + (c * kRowsB + row) * kRowF + (side ? kColX0 + kTileX : kColX0 - 1),
-                        ufield + c * n + zoff + rowoff[row] + halo_x[side]);
+        const unsigned so = (unsigned)((p % kRingB) * kPlaneB * sizeof(float));
+        if constexpr (vec) {
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[0] + so),
+                       "l"(csrc[0] + zoff) : "memory");
+          if (c1_is_row)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[1] + so),
+                         "l"(csrc[1] + zoff) : "memory");
+          else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cdst[1] + so),
+                         "l"(csrc[1] + zoff) : "memory");
+          if (c2_is_halo)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cdst[2] + so),
+                         "l"(csrc[2] + zoff) : "memory");
+          else if (c2_is_mu)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[2] + so),
+                         "l"(csrc[2] + zoff) : "memory");
+        } else {
+          float* slot = ring + (p % kRingB) * kPlaneB;
+          for (int q = threadIdx.x; q < kScalarCopies; q += kBlockB) {
+            if (q < 3 * kRowsB * (kTileX + 2)) {
+              const int c = q / (kRowsB * (kTileX + 2)), rem = q - c * (kRowsB * (kTileX + 2));
+              const int row = rem / (kTileX + 2), lx = rem - row * (kTileX + 2);
+              cp_async4(slot + (c * kRowsB + row) * kRowF + kColX0 - 1 + lx,
+                        ufield + c * n + zoff + rowoff[row] + wrap_index(x0 - 1 + lx, P.nx));
+            } else {  // mu_local of the tile (clamped to the domain; unused outside)
+              const int j = q - 3 * kRowsB * (kTileX + 2);
+              const int row = j / kTileX, lx = j - row * kTileX;
+              const int gx = min(x0 + lx, P.nx - 1), gy = min(y0 + row, P.ny - 1);
+              cp_async4(slot + kPlaneU + j, ufield + 3 * n + zoff + (long long)gy * P.nx + gx);
             }
           }
-        } else {
-          for (int q = threadIdx.x; q < kScalarCopies; q += kBlockB) {
-            const int c = q / (kRowsB * (kTileX + 2)), rem = q - c * (kRowsB * (kTileX + 2));
-            const int row = rem / (kTileX + 2), lx = rem - row * (kTileX + 2);
-            cp_async4(slot + (c * kRowsB + row) * kRowF + kColX0 - 1 + lx,
-                      ufield + c * n + zoff + rowoff[row] + wrap_index(x0 - 1 + lx, P.nx));
-          }
         }
+        zoff += nxy;
+        if (zoff >= n) zoff -= n;
       }
       cp_async_commit();  // an empty group past the last plane keeps the count uniform
     };
@@ -193,18 +253,6 @@ __global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
     const bool row_ok = y < P.ny;
     int nvalid = row_ok ? min(kCells, P.nx - xa) : 0;
     if (nvalid < 0) nvalid = 0;
-    // mu_local of the own cells at plane z (direct loads, one plane ahead)
-    const long long own = (long long)y * P.nx + xa;
-    auto load_mu = [&](int z, float (&m)[kCells]) {
-      const long long o = (long long)z * nxy + own;
-      if (vec && row_ok) {
-        const float4 v = *reinterpret_cast<const float4*>(MU + o);
-        m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
-      } else {
-#pragma unroll
-        for (int j = 0; j < kCells; ++j) m[j] = j < nvalid ? MU[o + j] : 0.0f;
-      }
-    };
     // one-sided x differences at held ends: factor 2 on the one available difference
     float fx[kCells];
     bool own_l[kCells], own_r[kCells];
@@ -217,65 +265,94 @@ __global__ void __launch_bounds__(kBlockB) k_diag_b(const DomainConst P,
       fx[j] = !P.bc_x ? 1.0f : (span == 2 ? 1.0f : (span == 1 ? 2.0f : 0.0f));
     }
     const int hc = (ty + 1) * kRowF + kColX0 + kCells * tx;  // own first cell in a plane
-    float pu[3][kCells], cu[3][kCells], mu[kCells], mu_n[kCells];
+    // u of the own cells on three planes, in three register sets whose roles (z - 1, z,
+    // z + 1) rotate from plane to plane, so the march moves no registers
+    float ua[3][kCells], ub[3][kCells], uc[3][kCells];
     cp_async_wait<kRingB - 2>();  // planes 0 and 1
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float4 a = lds4(ring + 0 * kPlaneB + c * kRowsB * kRowF + hc);
-      const float4 b = lds4(ring + 1 * kPlaneB + c * kRowsB * kRowF + hc);
-      pu[c][0] = a.x; pu[c][1] = a.y; pu[c][2] = a.z; pu[c][3] = a.w;
-      cu[c][0] = b.x; cu[c][1] = b.y; cu[c][2] = b.z; cu[c][3] = b.w;
+      ldv(ring + 0 * kPlaneB + c * kRowsB * kRowF + hc, ua[c]);
+      ldv(ring + 1 * kPlaneB + c * kRowsB * kRowF + hc, ub[c]);
     }
-    load_mu(z0, mu);
-    for (int i = 0; i < z1 - z0; ++i) {
+    // FP32 sums of the products over two planes, added to the float-float totals
+    float ss = 0.0f, sd = 0.0f;
+    // one plane of the march: pu, cu hold u at z - 1 and z, nu receives z + 1
+    auto plane = [&](int i, const float (&pu)[3][kCells], const float (&cu)[3][kCells],
+                     float (&nu)[3][kCells]) {
       cp_async_wait<kRingB - 3>();  // planes up to i + 2 have landed (this thread's copies)
       __syncthreads();              // ... everyone's; and everyone is done with plane i
       issue(i + kRingB);            // into the slot of plane i
-      if (i + 1 < z1 - z0) load_mu(z0 + i + 1, mu_n);
       const float* S0 = ring + ((i + 1) % kRingB) * kPlaneB;  // plane z
       const float* SP = ring + ((i + 2) % kRingB) * kPlaneB;  // plane z + 1
-      float d[3][3][kCells];  // d[a][b][j]: unscaled central difference of u_b along a
+      float mu[kCells];
+      ldv(S0 + kPlaneU + ty * kTileX + kCells * tx, mu);
+      // curl and divergence of the unscaled central differences, built component by
+      // component: w = (d_y u_z - d_z u_y, d_z u_x - d_x u_z, d_x u_y - d_y u_x)
+      float wx[kCells], wy[kCells], wz[kCells], dv[kCells];
+#pragma unroll
+      for (int j = 0; j < kCells; ++j) wx[j] = wy[j] = wz[j] = dv[j] = 0.0f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float* C0 = S0 + c * kRowsB * kRowF + hc;
-        const float4 nu = lds4(SP + c * kRowsB * kRowF + hc);
-        const float4 ym = lds4(C0 - kRowF), yp = lds4(C0 + kRowF);
+        float ymv[kCells], ypv[kCells];
+        ldv(SP + c * kRowsB * kRowF + hc, nu[c]);
+        ldv(C0 - kRowF, ymv);
+        ldv(C0 + kRowF, ypv);
         const float xl = C0[-1], xr = C0[kCells];
-        const float nv[kCells] = {nu.x, nu.y, nu.z, nu.w};
-        const float ymv[kCells] = {ym.x, ym.y, ym.z, ym.w}, ypv[kCells] = {yp.x, yp.y, yp.z, yp.w};
 #pragma unroll
         for (int j = 0; j < kCells; ++j) {
           float right = j + 1 < kCells ? cu[c][j + 1] : xr;
           float left = j > 0 ? cu[c][j - 1] : xl;
-          if (own_r[j]) right = cu[c][j];
-          if (own_l[j]) left = cu[c][j];
-          d[0][c][j] = mul(sub(right, left), fx[j]);
-          d[1][c][j] = sub(ypv[j], ymv[j]);
-          d[2][c][j] = sub(nv[j], pu[c][j]);
-        }
-#pragma unroll
-        for (int j = 0; j < kCells; ++j) {  // march: z becomes z - 1, z + 1 becomes z
-          pu[c][j] = cu[c][j];
-          cu[c][j] = nv[j];
+          float dx_;
+          if (P.bc_x) {
+            if (own_r[j]) right = cu[c][j];
+            if (own_l[j]) left = cu[c][j];
+            dx_ = mul(sub(right, left), fx[j]);
+          } else {
+            dx_ = sub(right, left);
+          }
+          const float dy_ = sub(ypv[j], ymv[j]);
+          const float dz_ = sub(nu[c][j], pu[c][j]);
+          if (c == 0) {
+            dv[j] = add(dv[j], dx_);
+            wz[j] = sub(wz[j], dy_);
+            wy[j] = add(wy[j], dz_);
+          } else if (c == 1) {
+            wz[j] = add(wz[j], dx_);
+            dv[j] = add(dv[j], dy_);
+            wx[j] = sub(wx[j], dz_);
+          } else {
+            wy[j] = sub(wy[j], dx_);
+            wx[j] = add(wx[j], dy_);
+            dv[j] = add(dv[j], dz_);
+          }
         }
       }
-      float ss = 0.0f, sd = 0.0f;
 #pragma unroll
       for (int j = 0; j < kCells; ++j) {
         if (j < nvalid) {
-          const float wx = sub(d[1][2][j], d[2][1][j]), wy = sub(d[2][0][j], d[0][2][j]),
-                      wz = sub(d[0][1][j], d[1][0][j]);
-          const float div = add(add(d[0][0][j], d[1][1][j]), d[2][2][j]);
-          ss = fma_(mu[j], fma_(wz, wz, fma_(wy, wy, mul(wx, wx))), ss);
-          sd = fma_(mu[j], mul(div, div), sd);
+          ss = fma_(mu[j], fma_(wz[j], wz[j], fma_(wy[j], wy[j], mul(wx[j], wx[j]))), ss);
+          sd = fma_(mu[j], mul(dv[j], dv[j]), sd);
         }
       }
-      ff_add(acc[0], mul(ss, s2));
-      ff_add(acc[1], mul(sd, s2));
-#pragma unroll
-      for (int j = 0; j < kCells; ++j) mu[j] = mu_n[j];
+      if (i & 1) {
+        ff_add(acc[0], mul(ss, s2));
+        ff_add(acc[1], mul(sd, s2));
+        ss = sd = 0.0f;
+      }
+    };
+    const int nzc = z1 - z0;
+    for (int i = 0; i < nzc; i += 6) {  // period of the register roles (3) and of the sums (2)
+      plane(i, ua, ub, uc);
+      if (i + 1 < nzc) plane(i + 1, ub, uc, ua);
+      if (i + 2 < nzc) plane(i + 2, uc, ua, ub);
+      if (i + 3 < nzc) plane(i + 3, ua, ub, uc);
+      if (i + 4 < nzc) plane(i + 4, ub, uc, ua);
+      if (i + 5 < nzc) plane(i + 5, uc, ua, ub);
     }
+    ff_add(acc[0], mul(ss, s2));  // an odd plane count leaves one plane's sums
+    ff_add(acc[1], mul(sd, s2));
     cp_async_wait<0>();
     __syncthreads();  // the next item refills every slot and the row table
   }
@@ -303,17 +380,32 @@ constexpr size_t kDiagBSmem = sizeof(float) * kRingB * kPlaneB;
 
 // Grid of pass B: the blocks resident on the device at once (one wave), at most
 // kDiagBlocks (the partials buffer holds that many).
+template <bool kVec>
 int diag_b_grid() {
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_diag_b<kVec>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kDiagBSmem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_b, kBlockB, kDiagBSmem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_b<kVec>, kBlockB, kDiagBSmem) !=
           cudaSuccess) {
     cudaGetLastError();
     return kDiagBlocks;
   }
   const int g = sms * per_sm;
   return g < 1 ? 1 : (g > kDiagBlocks ? kDiagBlocks : g);
+}
+
+// Pass B into pb; returns its grid (the number of records written).
+int launch_b(const DomainConst& P, const float* ufield, double* pb, cudaStream_t s) {
+  if (P.nx % kTileX == 0) {
+    const int g = diag_b_grid<true>();
+    k_diag_b<true><<<g, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+    return g;
+  }
+  const int g = diag_b_grid<false>();
+  k_diag_b<false><<<g, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+  return g;
 }
 
 // Fixed-order FP64 reduction of the block records of both passes (nblocks records of
@@ -395,8 +487,7 @@ cudaError_t launch_diag(const DomainConst& P, int store, int parity, const void*
     case 1: launch_a_store<__half>(P, parity, pop, ghost, ufield, pa, s); break;
     default: launch_a_store<__nv_bfloat16>(P, parity, pop, ghost, ufield, pa, s); break;
   }
-  const int gb = diag_b_grid();
-  k_diag_b<<<gb, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+  const int gb = launch_b(P, ufield, pb, s);
   k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, gb, out16);
   return cudaGetLastError();
 }
@@ -407,8 +498,7 @@ cudaError_t launch_diag_records(const DomainConst& P, const float* rec, long lon
   double* pa = partials;
   double* pb = partials + (long long)kDiagBlocks * kDiagA;
   k_diag_records<<<kDiagBlocks, kBlock, 0, s>>>(rec, nrec, pa);
-  const int gb = diag_b_grid();
-  k_diag_b<<<gb, kBlockB, kDiagBSmem, s>>>(P, ufield, pb);
+  const int gb = launch_b(P, ufield, pb, s);
   k_diag_final<<<1, kBlock, 0, s>>>(P, pa, pb, kDiagBlocks, gb, out16);
   return cudaGetLastError();
 }
