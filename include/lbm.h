@@ -213,13 +213,16 @@ lbm_status lbm_init_riemann(lbm_handle* h, int axis, int i_split, const double l
 
 /* Equilibrium from caller fields [5][cells] = rho, u_x, u_y, u_z, p in `dtype`
  * (LBM_DT_F32 or LBM_DT_F64) on the host or the device. Q_ref = (mean rho, 0, 0, 0,
- * mean of p/(gamma-1) + rho|u|^2/2). */
+ * mean of p/(gamma-1) + rho|u|^2/2), the means taken over every cell of domains of up
+ * to 2^20 cells and, for larger ones, over a fixed sample of about 2^20 cells (every
+ * s-th run of 32 consecutive cells, s = floor(runs / 2^15)): the storage only needs a
+ * reference near the data, and the sample saves a second full read of the fields. */
 lbm_status lbm_init_fields(lbm_handle* h, const void* fields, int src_on_device, int dtype);
 
 /* Equilibrium from caller zeroth moments [14][cells] (rho, rho u, E, tau, q; the
  * field order above) in `dtype` on the host or the device, e.g. a state whose stress
  * and heat flux start at their Newtonian and Fourier values (Becker's shock,
- * Sec. 3.1). Q_ref = (mean rho, 0, 0, 0, mean E). */
+ * Sec. 3.1). Q_ref = (mean rho, 0, 0, 0, mean E), means as for lbm_init_fields. */
 lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int dtype);
 
 /* ---- the hot path ------------------------------------------------------------ */

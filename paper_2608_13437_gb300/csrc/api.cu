@@ -537,7 +537,8 @@ static lbm_status init_from_fields(lbm_handle* h, const void* fields, int src_on
   if (e != cudaSuccess) {
     st = fail(LBM_E_CUDA, "field means failed: %s", cudaGetErrorString(e));
   } else {
-    const double rho_ref = sums[0] / (double)h->ncell, E_ref = sums[1] / (double)h->ncell;
+    const double cnt = (double)field_sample(h->ncell).cells;
+    const double rho_ref = sums[0] / cnt, E_ref = sums[1] / cnt;
     if (!std::isfinite(rho_ref) || !std::isfinite(E_ref)) {
       st = fail(LBM_E_INVAL, "initial fields contain non-finite values");
     } else {

@@ -254,17 +254,23 @@ __global__ void __launch_bounds__(128) k_init(const DomainConst P, const InitSpe
 
 constexpr int kMeanBlocks = (kFieldSumDoubles - 2) / 2, kMeanThreads = 256;
 
-// Sums of rho and E of the caller's fields in a fixed order: per thread as float-float
-// pairs (E = p/(gamma - 1) + rho|u|^2/2 per cell in float-float), widened to FP64 once
-// per thread, then a shared-memory tree per block and the blocks in order, so Q_ref is
-// reproducible.
+// Sums of rho and E of the caller's fields over the sample of field_sample(), in a
+// fixed order: per thread as float-float pairs (E = p/(gamma - 1) + rho|u|^2/2 per cell
+// in float-float), widened to FP64 once per thread, then a shared-memory tree per block
+// and the blocks in order, so Q_ref is reproducible. Sampled runs are 32 consecutive
+// cells (128-byte reads of each field).
 __global__ void __launch_bounds__(kMeanThreads) k_field_sums(const DomainConst P, const InitSpec sp,
+                                                             long long run_stride,
                                                              double* __restrict__ partials) {
   __shared__ double sh[2][kMeanThreads];
   FF s_rho{0.0f, 0.0f}, s_E{0.0f, 0.0f};
   const long long n = P.ncell;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
-       cell += (long long)gridDim.x * blockDim.x) {
+  const long long runs = (n + kTile - 1) / kTile;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;; t += (long long)gridDim.x * blockDim.x) {
+    const long long run = (t / kTile) * run_stride;
+    if (run >= runs) break;
+    const long long cell = run * kTile + (t % kTile);
+    if (cell >= n) continue;
     const FF rho = load_ff(sp, cell);
     ff_merge(s_rho, rho);
     if (sp.kind == 3) {
@@ -389,11 +395,22 @@ cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, i
   return cudaGetLastError();
 }
 
+FieldSample field_sample(long long ncell) {
+  const long long runs = (ncell + kTile - 1) / kTile;
+  FieldSample f;
+  f.run_stride = runs > kSampleRuns ? runs / kSampleRuns : 1;
+  f.cells = 0;
+  for (long long r = 0; r < runs; r += f.run_stride)
+    f.cells += (r + 1) * kTile <= ncell ? kTile : ncell - r * kTile;
+  return f;
+}
+
 cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
                                cudaStream_t s) {
   // sums holds 2 results followed by 2 * kMeanBlocks partials
   double* partials = sums + 2;
-  k_field_sums<<<kMeanBlocks, kMeanThreads, 0, s>>>(P, spec, partials);
+  k_field_sums<<<kMeanBlocks, kMeanThreads, 0, s>>>(P, spec, field_sample(P.ncell).run_stride,
+                                                     partials);
   k_field_sums_final<<<1, 32, 0, s>>>(partials, kMeanBlocks, sums);
   return cudaGetLastError();
 }

@@ -102,8 +102,17 @@ void fields_spec(double gamma, int kind, const void* fields, int f64, InitSpec* 
 // the encoded populations (canonical slots) and the held-x ghost layers.
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
                         float* ghost, unsigned* maxbits, cudaStream_t s);
-// Sums of rho and E over the caller fields (kind 2 or 3) into sums[0..2), in a fixed
-// order; sums must hold kFieldSumDoubles doubles (the rest is block scratch).
+// The cells whose fields fix Q_ref: every cell of domains up to kSampleRuns runs of 32
+// cells (2^20 cells); beyond that every run_stride-th run of 32 consecutive cells, about
+// 2^20 cells in all (a reference near the data is all the shifted storage needs).
+constexpr long long kSampleRuns = 1LL << 15;
+struct FieldSample {
+  long long run_stride;  // sampled runs: 0, run_stride, 2 run_stride, ...
+  long long cells;       // cells in the sample
+};
+FieldSample field_sample(long long ncell);
+// Sums of rho and E over the sample of the caller fields (kind 2 or 3) into sums[0..2),
+// in a fixed order; sums must hold kFieldSumDoubles doubles (the rest is block scratch).
 constexpr int kFieldSumDoubles = 2 + 2 * 1216;
 cudaError_t launch_field_means(const DomainConst& P, const InitSpec& spec, double* sums,
                                cudaStream_t s);

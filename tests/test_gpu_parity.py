@@ -848,3 +848,30 @@ def test_init_matches_oracle_equilibrium(lbm, oracle_mod, case):
         worst = max(worst, err)
         assert err <= 8.0, (case, k, err)
     print(f"{case}: largest error {worst:.2f} units of the field's largest deviation")
+
+
+def test_init_fields_reference_from_sample(lbm):
+    """Above 2^20 cells the reference Q_ref of caller fields is the mean over every s-th
+    run of 32 consecutive cells (s = floor(runs / 2^15)): 128^3 cells give s = 2. Q_ref
+    equals that sample mean (numpy, FP64), and the initial zeroth moments equal the
+    fields' (rho, rho u, E) to FP32 rounding whatever the reference."""
+    n = 128
+    p = inputs.tgv_params(n)
+    s = inputs.random_smooth_state(n, n, n, seed=53, amp=0.2)
+    f = [np.asarray(s[k], dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "p")]
+    dom = lbm.Domain(p)
+    dom.init_fields(*f, dtype=np.float32)
+    info = dom.info()
+    rho, ux, uy, uz, pr = [a.astype(np.float64).ravel() for a in f]
+    E = pr / (p["gamma"] - 1.0) + 0.5 * rho * (ux * ux + uy * uy + uz * uz)
+    runs = n ** 3 // 32
+    stride = runs // 2 ** 15
+    assert stride == 2
+    idx = (np.arange(0, runs, stride)[:, None] * 32 + np.arange(32)[None, :]).ravel()
+    assert info["rho_ref"] == pytest.approx(np.float32(rho[idx].mean()), rel=1e-7)
+    assert info["E_ref"] == pytest.approx(np.float32(E[idx].mean()), rel=1e-7)
+    Q = dom.moments()
+    dom.close()
+    want = [rho, rho * ux, rho * uy, rho * uz, E]
+    for k, w in enumerate(want):
+        assert rel_l2(Q[k].ravel(), w) < 3e-7, k
