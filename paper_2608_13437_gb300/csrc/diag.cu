@@ -111,6 +111,8 @@ constexpr int kPlaneU = 3 * kRowsB * kRowF; // floats of u on one plane (three c
 constexpr int kPlaneB = kPlaneU + kTileX * kTileY;  // ... followed by mu_local of the tile
 constexpr int kVecRows = 3 * kRowsB * (kTileX / 4), kVecHalo = 3 * kRowsB * 2;
 constexpr int kVecMu = kTileY * (kTileX / 4);
+constexpr int kVecCopies = kVecRows + kVecHalo + kVecMu;
+constexpr int kMaxCopies = (kVecCopies + kBlockB - 1) / kBlockB;  // per thread and plane
 constexpr int kScalarCopies = 3 * kRowsB * (kTileX + 2) + kTileX * kTileY;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
@@ -170,23 +172,29 @@ __global__ void __launch_bounds__(kBlockB, 4) k_diag_b(const DomainConst P,
     if (threadIdx.x == kRowsB + 1) halo_x[1] = wrap_index(x0 + kTileX, P.nx);
     __syncthreads();
     // plane p of the column is z = z0 - 1 + p (wrapped), held in ring slot p % kRingB.
-    // Full rows: this thread's (at most 3) copies of every plane, fixed per item: copy 0
-    // a 16-byte u row chunk, copy 1 a u row chunk or an x-halo value, copy 2 an x-halo
-    // value, a 16-byte mu row chunk or none (432 + 108 + 128 = 668 copies over 256
-    // threads).
-    static_assert(kBlockB == 256 && kVecRows == 432 && kVecHalo == 108 && kVecMu == 128,
-                  "copy split");
-    const float* csrc[3] = {ufield, ufield, ufield};
-    unsigned cdst[3] = {0u, 0u, 0u};
+    // Full rows: this thread's copies of every plane (16-byte u row chunks, 4-byte
+    // x-halo values, 16-byte mu_local row chunks, kVecCopies in all over the block),
+    // fixed per item: source without the plane offset, shared-memory destination in
+    // slot 0, size in bytes (0: none).
+    const float* csrc[kMaxCopies];
+    unsigned cdst[kMaxCopies];
+    int cbytes[kMaxCopies];
+#pragma unroll
+    for (int k = 0; k < kMaxCopies; ++k) {
+      csrc[k] = ufield;
+      cdst[k] = 0u;
+      cbytes[k] = 0;
+    }
     if constexpr (vec) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kMaxCopies; ++k) {
         const int q = threadIdx.x + k * kBlockB;
         if (q < kVecRows) {
           const int c = q / (kRowsB * 8), rem = q - c * (kRowsB * 8);
           const int row = rem >> 3, ch = rem & 7;
           csrc[k] = ufield + c * n + rowoff[row] + x0 + 4 * ch;
           cdst[k] = (unsigned)__cvta_generic_to_shared(ring + (c * kRowsB + row) * kRowF + kColX0 + 4 * ch);
+          cbytes[k] = 16;
         } else if (q < kVecRows + kVecHalo) {
           const int h = q - kVecRows;
           const int c = h / (kRowsB * 2), rem = h - c * (kRowsB * 2);
@@ -194,38 +202,31 @@ __global__ void __launch_bounds__(kBlockB, 4) k_diag_b(const DomainConst P,
           csrc[k] = ufield + c * n + rowoff[row] + halo_x[side];
           cdst[k] = (unsigned)__cvta_generic_to_shared(
               ring + (c * kRowsB + row) * kRowF + (side ? kColX0 + kTileX : kColX0 - 1));
-        } else if (q < kVecRows + kVecHalo + kVecMu) {  // mu_local rows (no halo)
+          cbytes[k] = 4;
+        } else if (q < kVecCopies) {  // mu_local rows (no halo)
           const int m = q - kVecRows - kVecHalo;
           const int row = m >> 3, ch = m & 7;
           const int gy = min(y0 + row, P.ny - 1);
           csrc[k] = ufield + 3 * n + (long long)gy * P.nx + x0 + 4 * ch;
           cdst[k] = (unsigned)__cvta_generic_to_shared(ring + kPlaneU + row * kTileX + 4 * ch);
+          cbytes[k] = 16;
         }
       }
     }
-    const bool c1_is_row = threadIdx.x + kBlockB < kVecRows;
-    const int q2 = threadIdx.x + 2 * kBlockB;
-    const bool c2_is_halo = q2 < kVecRows + kVecHalo;
-    const bool c2_is_mu = !c2_is_halo && q2 < kVecRows + kVecHalo + kVecMu;
     long long zoff = (long long)wrap_index(z0 - 1, P.nz) * nxy;  // of the next plane to issue
     auto issue = [&](int p) {
       if (p < np) {
         const unsigned so = (unsigned)((p % kRingB) * kPlaneB * sizeof(float));
         if constexpr (vec) {
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[0] + so),
-                       "l"(csrc[0] + zoff) : "memory");
-          if (c1_is_row)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[1] + so),
-                         "l"(csrc[1] + zoff) : "memory");
-          else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cdst[1] + so),
-                         "l"(csrc[1] + zoff) : "memory");
-          if (c2_is_halo)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cdst[2] + so),
-                         "l"(csrc[2] + zoff) : "memory");
-          else if (c2_is_mu)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[2] + so),
-                         "l"(csrc[2] + zoff) : "memory");
+#pragma unroll
+          for (int k = 0; k < kMaxCopies; ++k) {
+            if (cbytes[k] == 16)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cdst[k] + so),
+                           "l"(csrc[k] + zoff) : "memory");
+            else if (cbytes[k] == 4)
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cdst[k] + so),
+                           "l"(csrc[k] + zoff) : "memory");
+          }
         } else {
           float* slot = ring + (p % kRingB) * kPlaneB;
           for (int q = threadIdx.x; q < kScalarCopies; q += kBlockB) {
