@@ -337,15 +337,16 @@ def test_step_diag_matches_oracle_on_tgv(lbm, oracle_mod):
     dom.close()
 
 
-@pytest.mark.parametrize("component,T_axis", [(0, 1), (1, 2)])
-def test_diag_closed_forms_on_wave(lbm, component, T_axis):
+@pytest.mark.parametrize("component,T_axis,nx", [(0, 1, 48), (1, 2, 48), (0, 2, 64), (2, 1, 64)])
+def test_diag_closed_forms_on_wave(lbm, component, T_axis, nx):
     """Both diagnostic paths (lbm_diag, and lbm_step_diag inside the first step) on
     one velocity wave u_c = A sin(k x) with a temperature varying along another axis
     (Sutherland viscosity) against the closed forms the oracle is pinned to (Eq. 7:
     2/3 mbar A^2 (sin(k dx)/dx)^2 compressive, 1/2 mbar A^2 (sin(k dx)/dx)^2 shear;
     max Mach A / sqrt(gamma T_min); max CFL (A + sqrt(gamma T_max)) dt/dx), at the FP32
-    tolerances of the diagnostics tests."""
-    nx, ny, nz, k, A, rho0, T0, mu, T_ref = 48, 6, 5, 2, 0.3, 1.3, 0.9, 0.037, 0.8
+    tolerances of the diagnostics tests. nx = 48 takes the gradient pass's element-copy
+    form, nx = 64 its form for rows of whole 32-cell tiles."""
+    ny, nz, k, A, rho0, T0, mu, T_ref = 6, 5, 2, 0.3, 1.3, 0.9, 0.037, 0.8
     p = inputs.tgv_params(16)
     p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / nx, mu=mu, T_ref=T_ref, sutherland=1)
     f = inputs.separable_wave_fields(nx, ny, nz, A, k, rho0, T0, 0.35, component, T_axis)
@@ -875,3 +876,24 @@ def test_init_fields_reference_from_sample(lbm):
     want = [rho, rho * ux, rho * uy, rho * uz, E]
     for k, w in enumerate(want):
         assert rel_l2(Q[k].ravel(), w) < 3e-7, k
+
+
+@pytest.mark.parametrize("nx", [48, 64])
+def test_diag_held_ends_linear_profile(lbm, nx):
+    """Held x ends: the gradient pass differences one-sidedly at the end cells, so a
+    linear u_x = A x has div u = A in every cell and 4/3 <mu (div u)^2> = 4/3 mu A^2
+    (constant viscosity; the oracle is pinned to the same form), on both diagnostic
+    paths and both copy forms of the pass."""
+    ny, nz, A, rho0, T0, mu = 20, 3, 0.05, 1.1, 0.8, 0.021
+    p = inputs.sod_params(nx, ny=ny, nz=nz)
+    p.update(mu=mu, sutherland=0)
+    shape = (nz, ny, nx)
+    x = (np.arange(nx) + 0.5) / nx
+    ux = np.broadcast_to(A * x, shape)
+    for path in ("diag", "step_diag"):
+        dom = lbm.Domain(p)
+        dom.init_fields(np.full(shape, rho0), ux, 0.0, 0.0, np.full(shape, rho0 * T0))
+        d = dom.diag() if path == "diag" else dom.step_diag(1)
+        dom.close()
+        assert d["eps_d_raw"] == pytest.approx(4.0 / 3.0 * mu * A * A, rel=1e-5), path
+        assert abs(d["eps_s_raw"]) < 1e-9 * mu * A * A, path

@@ -213,3 +213,24 @@ def test_wave_diagnostics_closed_forms(oracle_mod, sutherland, dT, component, T_
     for key in ("sum_mx", "sum_my", "sum_mz"):
         assert abs(d[key]) < 1e-12
     assert d["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("nx", [16, 2])
+def test_held_ends_one_sided_differences(oracle_mod, nx):
+    """With held x ends the x derivative is one-sided at the two end cells. A linear
+    velocity u_x = A x is differentiated exactly by both the central and the one-sided
+    differences, so div u = A in every cell and 4/3 <mu (div u)^2> = 4/3 mu A^2 (constant
+    viscosity), with no curl. A one-sided difference divided by 2 dx (or 0) at an end
+    cell, or a wrapped (periodic) neighbour there, breaks it; nx = 2 has only end
+    cells."""
+    ny, nz, A, rho0, T0, mu = 3, 2, 0.05, 1.1, 0.8, 0.021
+    p = inputs.sod_params(nx, ny=ny, nz=nz)
+    p.update(mu=mu, sutherland=0)
+    o = make_oracle(p)
+    x = (np.arange(nx) + 0.5) / nx
+    shape = (nz, ny, nx)
+    ux = np.broadcast_to(A * x, shape)
+    o.init_fields(np.full(shape, rho0), ux, 0.0, 0.0, np.full(shape, rho0 * T0))
+    d = o.diag()
+    assert d["eps_d_raw"] == pytest.approx(4.0 / 3.0 * mu * A * A, rel=1e-12)
+    assert abs(d["eps_s_raw"]) < 1e-25
