@@ -884,7 +884,7 @@ def test_diag_held_ends_linear_profile(lbm, nx):
     linear u_x = A x has div u = A in every cell and 4/3 <mu (div u)^2> = 4/3 mu A^2
     (constant viscosity; the oracle is pinned to the same form), on both diagnostic
     paths and both copy forms of the pass."""
-    ny, nz, A, rho0, T0, mu = 20, 3, 0.05, 1.1, 0.8, 0.021
+    ny, nz, A, rho0, T0, mu = 20, 3, 0.5, 1.1, 0.8, 0.021
     p = inputs.sod_params(nx, ny=ny, nz=nz)
     p.update(mu=mu, sutherland=0)
     shape = (nz, ny, nx)
@@ -895,5 +895,6 @@ def test_diag_held_ends_linear_profile(lbm, nx):
         dom.init_fields(np.full(shape, rho0), ux, 0.0, 0.0, np.full(shape, rho0 * T0))
         d = dom.diag() if path == "diag" else dom.step_diag(1)
         dom.close()
-        assert d["eps_d_raw"] == pytest.approx(4.0 / 3.0 * mu * A * A, rel=1e-5), path
+        # FP32 u differences of 2 A dx = 0.02 carry relative errors of about 1e-6
+        assert d["eps_d_raw"] == pytest.approx(4.0 / 3.0 * mu * A * A, rel=2e-5), path
         assert abs(d["eps_s_raw"]) < 1e-9 * mu * A * A, path
