@@ -28,15 +28,28 @@ FIELD_NAMES = ("rho", "mx", "my", "mz", "E", "txx", "tyy", "tzz", "txy", "txz", 
                "qx", "qy", "qz")
 
 
+# LBM_ORACLE_SANITIZED=1 selects a second build with AddressSanitizer and
+# UndefinedBehaviorSanitizer (single-threaded, aborting on the first finding); a process
+# that loads it must preload the ASan runtime (the sanitizer test does).
+_SANITIZED = os.environ.get("LBM_ORACLE_SANITIZED") == "1"
+if _SANITIZED:
+    _LIB = os.path.join(_BUILD, "liboracle_sanitized.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so in place; returns its path."""
+    """Compile liboracle.so (or the sanitized variant) in place; returns its path."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
-           "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC]
+    if _SANITIZED:
+        cmd = ["g++", "-O1", "-g", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas", "-fsanitize=address,undefined",
+               "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer", "-o", tmp, _SRC]
+    else:
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+               "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
