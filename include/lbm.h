@@ -353,6 +353,16 @@ lbm_status lbm_set_prefetch(lbm_handle* h, int tiles);
  * lbm_step refuses to run until a re-init. LBM_E_INVAL for a plain form. */
 lbm_status lbm_test_skip_copy(lbm_handle* h);
 
+/* Memory-safety test hook (no counterpart in the paper; a stand-in for a GPU memory
+ * checker). A build compiled with LBM_CHECKED tests every population tile and ghost
+ * address its kernels form against the buffer before using it; an address outside
+ * adds 1 to a per-handle (per-batch) count and the access is dropped (a load reads
+ * zero) instead of faulting. These calls return that count, accumulated since
+ * create, in *count (synchronising the stream). Other builds set *count = 0 and return
+ * LBM_E_STATE. LBM_E_INVAL for a NULL argument. */
+lbm_status lbm_check_count(const lbm_handle* h, unsigned long long* count);
+lbm_status lbm_batch_check_count(const lbm_batch* b, unsigned long long* count);
+
 /* Codec test hook: the 16-bit store conversion of the step kernels (the encoding of the
  * reference-shifted deviations of Sec. 2.2 into FP16 or BF16; no counterpart in the
  * paper, which stores FP32) applied at unit scale to npair pairs of floats:

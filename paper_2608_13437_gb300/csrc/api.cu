@@ -401,6 +401,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_handle** out) {
   }
   if (cudaMemset(h->ghost, 0, ghost_bytes) != cudaSuccess || cudaMemset(h->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "cudaMemset failed"));
+  h->P.check = h->flag + 2;  // word 2 of the flag block: the checked build's address count
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "cudaStreamCreate failed"));
   *out = h;
@@ -985,6 +986,21 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out) {
     out->prefetch_tiles = best_pf;
   }
   return LBM_OK;
+}
+
+lbm_status lbm_check_count(const lbm_handle* h, unsigned long long* count) {
+  if (!h || !count) return fail(LBM_E_INVAL, "NULL argument");
+#ifdef LBM_CHECKED
+  LBM_ON_DEVICE(h->device);
+  unsigned v = 0;
+  LBM_CUDA(cudaMemcpyAsync(&v, h->flag + 2, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  *count = v;
+  return LBM_OK;
+#else
+  *count = 0;
+  return fail(LBM_E_STATE, "not a checked build (compiled without LBM_CHECKED)");
+#endif
 }
 
 lbm_status lbm_test_skip_copy(lbm_handle* h) {

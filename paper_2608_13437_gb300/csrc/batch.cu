@@ -404,6 +404,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       cudaMemcpy(b->d_tiles, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->flag, 0, 64) != cudaSuccess)
     return cleanup(fail(LBM_E_CUDA, "batch table upload failed"));
+  for (int d = 0; d < n; ++d) b->P[d].check = b->flag + 2;  // the checked build's address count
   lbm_status s = upload_consts(b);
   if (s != LBM_OK) return cleanup(s);
   s = size_grid(b);
@@ -650,6 +651,21 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps_per_trial, int* tile_cells
   if (ms_per_step) *ms_per_step = best;
   if (prefetch_tiles) *prefetch_tiles = best_pf;
   return LBM_OK;
+}
+
+lbm_status lbm_batch_check_count(const lbm_batch* b, unsigned long long* count) {
+  if (!b || !count) return fail(LBM_E_INVAL, "NULL argument");
+#ifdef LBM_CHECKED
+  LBM_ON_DEVICE(b->device);
+  unsigned v = 0;
+  LBM_CUDA(cudaMemcpyAsync(&v, b->flag + 2, sizeof(v), cudaMemcpyDeviceToHost, b->stream));
+  LBM_CUDA(cudaStreamSynchronize(b->stream));
+  *count = v;
+  return LBM_OK;
+#else
+  *count = 0;
+  return fail(LBM_E_STATE, "not a checked build (compiled without LBM_CHECKED)");
+#endif
 }
 
 lbm_status lbm_batch_set_prefetch(lbm_batch* b, int tiles) {

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(128) k_init(const DomainConst P, const InitSpe
         for (int i = 0; i < kQ; ++i) mx[k] = fmaxf(mx[k], fabsf(dev[k][i]));
       continue;
     }
+    if (!LBM_CHECK(P, cell < P.ntile * kTile)) continue;
     S* base = pop + tile_start(cell);
     const int lane = (int)(cell & (kTile - 1));
 #pragma unroll

@@ -170,6 +170,7 @@ __global__ void k_plane(const DomainConst P, T* __restrict__ pop, int z, int slo
        r += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(r / plane);
     const long long cell = r - k * plane + plane * z;
+    if (!LBM_CHECK(P, cell >= 0 && cell < P.ncell)) continue;
     const long long at = pop_index(cell, k, slot);
     if (set) pop[at] = buf[r];
     else buf[r] = pop[at];

@@ -50,7 +50,22 @@ struct DomainConst {
   int sround;         // 16-bit storage rounds stochastically (1) or to nearest (0)
   int pf_tiles;       // L2 prefetch distance of the plain step kernel on whole-tile rows (0: off)
   double dx64;        // dx in FP64 (the diagnostics' gradient pass takes 1/dx from it)
+  unsigned* check;    // checked builds: count of population addresses found outside the buffer
 };
+
+// Checked builds (-DLBM_CHECKED): every population tile and ghost-plane address is
+// tested before use; one outside the buffer adds 1 to *P.check and the access is
+// dropped (a load reads zero), so a bad index shows as a count instead of a fault.
+// Other builds compile the test away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool lbm_check(const DomainConst& P, bool ok) {
+  if (!ok && P.check) atomicAdd(P.check, 1u);
+  return ok;
+}
+#define LBM_CHECK(P, cond) ::lbm::lbm_check((P), (cond))
+#else
+#define LBM_CHECK(P, cond) true
+#endif
 
 // ---------------------------------------------------------------- storage codecs
 // Scalar codecs (dec/enc) and the vector forms used by the step kernel: V4 holds
@@ -260,7 +275,8 @@ __device__ __forceinline__ CellIndex make_index(const DomainConst& P, int x, int
 // Cell and slot from which direction i of this cell is read at `parity`.
 __device__ __forceinline__ long long read_pos(const DomainConst& P, const CellIndex& c, int parity,
                                               int k, int i) {
-  const long long cell = parity ? c.nb[opp(i)] : c.own;
+  long long cell = parity ? c.nb[opp(i)] : c.own;
+  if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) cell = 0;
   const int slot = parity ? opp(i) : i;
   return pop_index(cell, k, slot);
 }
@@ -275,6 +291,7 @@ __device__ __forceinline__ float ghost_value(const DomainConst& P, const float* 
                                              const CellIndex& c, int k, int i) {
   const long long planes = (long long)P.ny * P.nz;
   const int side = (i == 1) ? 0 : 1;
+  if (!LBM_CHECK(P, c.plane >= 0 && c.plane < planes)) return 0.0f;
   return ghost[((long long)side * kF + k) * planes + c.plane];
 }
 
@@ -290,6 +307,11 @@ __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restr
   for (int i = 0; i < kQ; ++i) {
     const long long cell = PARITY ? c.nb[opp(i)] : c.own;
     const int slot = PARITY ? opp(i) : i;
+    if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) {
+#pragma unroll
+      for (int k = 0; k < kF; ++k) d[k][i] = 0.0f;
+      continue;
+    }
     const S* base = pop + tile_start(cell);
     const int lane = (int)(cell & (kTile - 1));
     float v[kF];
@@ -377,6 +399,7 @@ __device__ __forceinline__ void store_cell(const DomainConst& P, S* __restrict__
   for (int i = 0; i < kQ; ++i) {
     const long long cell = PARITY ? c.nb[i] : c.own;
     const int slot = PARITY ? i : opp(i);
+    if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) continue;
     store_dir<S>(P, pop + tile_start(cell), slot, (int)(cell & (kTile - 1)), d, i,
                  SR ? &dz : nullptr);
   }

@@ -94,6 +94,11 @@ __device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __
     int ln = lane;
     if (PARITY && i > 0) link_tile(T, i, -1, lane, tile, ln);
     const int slot = PARITY ? opp(i) : i;
+    if (!LBM_CHECK(P, tile >= 0 && tile < P.ntile)) {
+#pragma unroll
+      for (int k = 0; k < kF; ++k) d[k][i] = 0.0f;
+      continue;
+    }
     const S* base = pop + tile * kTileElems;
     float v[kF];
 #pragma unroll
@@ -121,6 +126,7 @@ __device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restr
     long long tile = T.t;
     int ln = lane;
     if (PARITY && i > 0) link_tile(T, i, +1, lane, tile, ln);
+    if (!LBM_CHECK(P, tile >= 0 && tile < P.ntile)) continue;
     store_dir<S>(P, pop + tile * kTileElems, PARITY ? i : opp(i), ln, d, i, SR ? &dz : nullptr);
   }
 }

@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
+# LBM_LIBRARY=checked selects the build with address checks (liblbm_checked.so; see
+# lbm_check_count in include/lbm.h); the default is the production build.
+LIB_VARIANT = os.environ.get("LBM_LIBRARY", "")
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_checked.so" if LIB_VARIANT == "checked" else "liblbm.so")
 
 LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NONFINITE, LBM_E_STATE, LBM_E_IO, LBM_E_TIMEOUT = range(8)
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
@@ -113,6 +116,8 @@ _SIGNATURES = {
     "lbm_batch_autotune": (_IP, [_VP, _IP, ctypes.POINTER(_IP), ctypes.POINTER(_IP),
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_IP)]),
     "lbm_batch_set_prefetch": (_IP, [_VP, _IP]),
+    "lbm_check_count": (_IP, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "lbm_batch_check_count": (_IP, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
 }
 
 
