@@ -898,3 +898,31 @@ def test_diag_held_ends_linear_profile(lbm, nx):
         # FP32 u differences of 2 A dx = 0.02 carry relative errors of about 1e-6
         assert d["eps_d_raw"] == pytest.approx(4.0 / 3.0 * mu * A * A, rel=2e-5), path
         assert abs(d["eps_s_raw"]) < 1e-9 * mu * A * A, path
+
+
+@pytest.mark.parametrize("nx", [1, 2, 3, 5])
+def test_held_x_degenerate_widths_match_oracle(lbm, oracle_mod, nx):
+    """Held x ends on the narrowest domains: every cell is an end cell (nx = 1, 2) or
+    next to one (3, 5), so the ghost inflow and the one-sided diagnostics carry the
+    whole update. A Riemann problem (split at nx // 2; nx = 1 holds one state) after 10
+    steps agrees with the oracle within the FP32 parity bar, and so do the
+    diagnostics."""
+    p = inputs.sod_params(nx, ny=3, nz=2)
+    p.update(dt=0.002)  # a time step valid for every width (dx = 1 / nx)
+    g = lbm.Domain(p)
+    g.init_riemann(0, nx // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    o = make_oracle(p)
+    o.init_riemann(0, nx // 2, inputs.SOD_LEFT, inputs.SOD_RIGHT)
+    g.step(10)
+    o.step(10)
+    pg, po = g.primitives(), o.primitives()
+    err = prim_errors(pg, po)
+    if nx == 1:  # one cell between equal ghosts stays at rest: u is zero on both sides
+        assert np.abs(pg[1:4]).max() < 1e-12 and np.abs(po[1:4]).max() < 1e-12
+        del err["u"]
+    assert max(err.values()) < 1e-5, err
+    dg, do = g.diag(), o.diag()
+    for k in ("sum_rho", "sum_E", "min_rho", "min_T", "max_cfl"):
+        assert dg[k] == pytest.approx(do[k], rel=2e-6), k
+    assert dg["eps_d_raw"] == pytest.approx(do["eps_d_raw"], rel=1e-4, abs=1e-12)
+    g.close()
