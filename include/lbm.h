@@ -197,7 +197,9 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info_t* out);
  * Each sets every cell's populations to the linear equilibrium of its state with
  * zero stress and heat flux (tau = q = 0), resets the step counter and the
  * non-finite flag, records the held-x ghost populations, and fixes the storage
- * reference Q_ref and (F16) the per-field scales s_k = max|f - w Q_ref| / 1024. */
+ * reference Q_ref and (F16) the per-field scales s_k = max|f - w Q_ref| / 1024.
+ * A state that is not finite in some cell gives LBM_E_INVAL and leaves the handle
+ * uninitialised. */
 
 /* Supersonic Taylor-Green vortex of Sec. 3.2 on a box of side nx*dx = 2 pi L:
  * u = U0 sin x cos y cos z, v = -U0 cos x sin y cos z, w = 0,

@@ -286,7 +286,7 @@ lbm_status run_init(lbm_handle* h, InitSpec& sp) {
   reset_scales(h);
   if (h->prm.store == LBM_STORE_F16) {
     LBM_CUDA(cudaMemsetAsync(h->maxbits, 0, kF * sizeof(unsigned), h->stream));
-    LBM_CUDA(launch_init(h->P, h->prm.store, sp, 0, h->pop, h->ghost, h->maxbits, h->stream));
+    LBM_CUDA(launch_init(h->P, h->prm.store, sp, 0, h->pop, h->ghost, h->maxbits, nullptr, h->stream));
     unsigned bits[kF];
     LBM_CUDA(cudaMemcpyAsync(bits, h->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -301,9 +301,18 @@ lbm_status run_init(lbm_handle* h, InitSpec& sp) {
       h->scale[k] = sk;
     }
   }
-  LBM_CUDA(launch_init(h->P, h->prm.store, sp, 1, h->pop, h->ghost, nullptr, h->stream));
+  // word 3 of the flag block: set by the kernel if the initial state is not finite
+  LBM_CUDA(cudaMemsetAsync(h->flag + 3, 0, sizeof(unsigned), h->stream));
+  LBM_CUDA(launch_init(h->P, h->prm.store, sp, 1, h->pop, h->ghost, nullptr, h->flag + 3, h->stream));
   LBM_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(unsigned), h->stream));
+  unsigned bad = 0;
+  LBM_CUDA(cudaMemcpyAsync(&bad, h->flag + 3, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (bad) {
+    h->initialized = false;
+    h->graphs_valid = false;
+    return fail(LBM_E_INVAL, "the initial state has non-finite values");
+  }
   h->step = 0;
   h->initialized = true;
   h->nonfinite = false;

@@ -457,7 +457,8 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
     for (int k = 0; k < kF; ++k) b->P[d].scale[k] = b->P[d].inv_scale[k] = 1.0f;
     if (b->store == LBM_STORE_F16) {  // per-field scale max|f - w Q_ref| / 1024, as for one domain
       LBM_CUDA(cudaMemsetAsync(b->d_maxbits, 0, kF * sizeof(unsigned), b->stream));
-      LBM_CUDA(launch_init(b->P[d], b->store, sp, 0, domain_pop(b, d), nullptr, b->d_maxbits, b->stream));
+      LBM_CUDA(launch_init(b->P[d], b->store, sp, 0, domain_pop(b, d), nullptr, b->d_maxbits, nullptr,
+                           b->stream));
       unsigned bits[kF];
       LBM_CUDA(cudaMemcpyAsync(bits, b->d_maxbits, sizeof(bits), cudaMemcpyDeviceToHost, b->stream));
       LBM_CUDA(cudaStreamSynchronize(b->stream));
@@ -469,7 +470,8 @@ lbm_status lbm_batch_init_tgv(lbm_batch* b, const double* U0, const double* M0, 
         b->P[d].inv_scale[k] = 1.0f / sk;
       }
     }
-    LBM_CUDA(launch_init(b->P[d], b->store, sp, 1, domain_pop(b, d), nullptr, nullptr, b->stream));
+    LBM_CUDA(launch_init(b->P[d], b->store, sp, 1, domain_pop(b, d), nullptr, nullptr, nullptr,
+                         b->stream));
   }
   lbm_status s = upload_consts(b);
   if (s != LBM_OK) return s;

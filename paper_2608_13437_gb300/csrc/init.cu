@@ -199,12 +199,14 @@ __device__ __forceinline__ void equilibrium_dev(const DomainConst& P, const Init
 }
 
 // mode 0: per-field max |d| into maxbits (for the FP16 scales); mode 1: write the
-// populations (canonical slots: slot i of a cell holds f_i) and the held-x ghosts.
-// Blocks of whole warps, so a warp covers one 32-cell tile.
+// populations (canonical slots: slot i of a cell holds f_i) and the held-x ghosts, and
+// set *bad (if given) when a cell's state is not finite. Blocks of whole warps, so a
+// warp covers one 32-cell tile.
 template <typename S>
 __global__ void __launch_bounds__(128) k_init(const DomainConst P, const InitSpec sp, int mode,
                                               S* __restrict__ pop, float* __restrict__ ghost,
-                                              unsigned* __restrict__ maxbits) {
+                                              unsigned* __restrict__ maxbits,
+                                              unsigned* __restrict__ bad) {
   const long long n = P.ncell;
   const long long planes = (long long)P.ny * P.nz;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -228,6 +230,12 @@ __global__ void __launch_bounds__(128) k_init(const DomainConst P, const InitSpe
 #pragma unroll
         for (int i = 0; i < kQ; ++i) mx[k] = fmaxf(mx[k], fabsf(dev[k][i]));
       continue;
+    }
+    if (bad) {  // a non-finite input or state ends up in the moments or the fluxes
+      float probe = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kF; ++k) probe += dev[k][1] + dev[k][2];
+      if (!isfinite(probe)) atomicOr(bad, 1u);
     }
     if (!LBM_CHECK(P, cell < P.ntile * kTile)) continue;
     S* base = pop + tile_start(cell);
@@ -385,13 +393,13 @@ void fields_spec(double gamma, int kind, const void* fields, int f64, InitSpec* 
 }
 
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
-                        float* ghost, unsigned* maxbits, cudaStream_t s) {
+                        float* ghost, unsigned* maxbits, unsigned* bad, cudaStream_t s) {
   const int block = 128;
   const int grid = grid_for(P.ncell, block);
   switch (store) {
-    case 0: k_init<float><<<grid, block, 0, s>>>(P, spec, mode, static_cast<float*>(pop), ghost, maxbits); break;
-    case 1: k_init<__half><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__half*>(pop), ghost, maxbits); break;
-    default: k_init<__nv_bfloat16><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__nv_bfloat16*>(pop), ghost, maxbits); break;
+    case 0: k_init<float><<<grid, block, 0, s>>>(P, spec, mode, static_cast<float*>(pop), ghost, maxbits, bad); break;
+    case 1: k_init<__half><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__half*>(pop), ghost, maxbits, bad); break;
+    default: k_init<__nv_bfloat16><<<grid, block, 0, s>>>(P, spec, mode, static_cast<__nv_bfloat16*>(pop), ghost, maxbits, bad); break;
   }
   return cudaGetLastError();
 }

@@ -99,9 +99,10 @@ void riemann_spec(const DomainConst& P, double gamma, int axis, int split, const
                   const double right[3], InitSpec* sp);
 void fields_spec(double gamma, int kind, const void* fields, int f64, InitSpec* sp);
 // mode 0: per-field max |f - w Q_ref| into maxbits[14] (float bits); mode 1: write
-// the encoded populations (canonical slots) and the held-x ghost layers.
+// the encoded populations (canonical slots) and the held-x ghost layers, and set *bad
+// (when not null) if some cell's state is not finite.
 cudaError_t launch_init(const DomainConst& P, int store, const InitSpec& spec, int mode, void* pop,
-                        float* ghost, unsigned* maxbits, cudaStream_t s);
+                        float* ghost, unsigned* maxbits, unsigned* bad, cudaStream_t s);
 // The cells whose fields fix Q_ref: every cell of domains up to kSampleRuns runs of 32
 // cells (2^20 cells); beyond that every run_stride-th run of 32 consecutive cells, about
 // 2^20 cells in all (a reference near the data is all the shifted storage needs).

@@ -926,3 +926,28 @@ def test_held_x_degenerate_widths_match_oracle(lbm, oracle_mod, nx):
         assert dg[k] == pytest.approx(do[k], rel=2e-6), k
     assert dg["eps_d_raw"] == pytest.approx(do["eps_d_raw"], rel=1e-4, abs=1e-12)
     g.close()
+
+
+@pytest.mark.parametrize("n,at", [(16, (3, 4, 5)), (128, (0, 0, 40))])
+def test_init_rejects_non_finite_fields(lbm, n, at):
+    """A non-finite value anywhere in the caller's fields makes the initialisation fail
+    with LBM_E_INVAL and leaves the handle uninitialised (steps are refused), also where
+    the cell lies outside the sample that fixes Q_ref (128^3: cell 40 is in run 1, and
+    only even runs are sampled); a valid initialisation afterwards works."""
+    p = inputs.tgv_params(n)
+    f = inputs.tgv_fields(n, dtype=np.float64)
+    dom = lbm.Domain(p)
+    for value in (np.nan, np.inf):
+        bad = f.copy()
+        bad[4][at] = value
+        with pytest.raises(lbm.LbmError) as ei:
+            dom.init_fields(*bad)
+        assert ei.value.status == lbm.LBM_E_INVAL
+        with pytest.raises(lbm.LbmError) as ei:
+            dom.step(1)
+        assert ei.value.status == lbm.LBM_E_STATE
+    dom.init_fields(*f)
+    dom.step(2)
+    dom.synchronize()
+    assert np.isfinite(dom.primitives()).all()
+    dom.close()
