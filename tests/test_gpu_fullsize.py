@@ -2,7 +2,8 @@
   * 512^3 TGV in the benchmark's launch configuration against the oracle on a light
     cone: after n steps a cell depends only on cells within n lattice steps, so the
     oracle recomputes a (B + 2n)^3 window of the same initial field and its central
-    B^3 cells must match the GPU's (sampled outputs at full size);
+    B^3 cells must match the GPU's (sampled outputs at full size), for FP32 and the
+    FP16 and BF16 storage modes;
   * the largest FP32 cube that fits (840^3) on light cones, interior and across the
     periodic corner;
   * 512^3: the TMA-staged step form against the plain kernel (bit for bit, on the
@@ -40,13 +41,16 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-@pytest.mark.parametrize("steps", [40, 41])
-def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps):
+@pytest.mark.parametrize("steps,store,bound", [(40, "f32", 1e-5), (41, "f32", 1e-5),
+                                               (40, "f16", 2e-3), (41, "bf16", 2e-2)])
+def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps, store, bound):
+    """FP32 within the parity bar; the 16-bit storage modes (the bench's FP16 and BF16
+    legs) within the bounds their 32^3 error tests state."""
     import torch
     n, B = 512, 12
     origin = (100, 250, 400)
     p = inputs.tgv_params(n)
-    dom = lbm.Domain(p)
+    dom = lbm.Domain(p, store=store)
     dom.init_tgv(1.0, 1.25, 1.0)
     dom.autotune(pairs_per_trial=2)  # the benchmark's configuration; re-init after
     dom.init_tgv(1.0, 1.25, 1.0)
@@ -66,7 +70,8 @@ def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps):
     o.step(steps)
     r = o.primitives()[:, steps:steps + B, steps:steps + B, steps:steps + B]
     errs = {"rho": rel_l2(g[0], r[0]), "u": rel_l2(g[1:4], r[1:4]), "T": rel_l2(g[4], r[4])}
-    assert max(errs.values()) < 1e-5, errs
+    print(f"512^3 {store} light cone after {steps} steps: {errs}")
+    assert max(errs.values()) < bound, errs
 
 
 def test_largest_fp32_domain_matches_oracle_on_light_cones(lbm, oracle_mod):
