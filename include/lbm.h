@@ -422,6 +422,12 @@ lbm_status lbm_batch_synchronize(lbm_batch* b);
 /* lbm_moments of one domain. */
 lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int dst_on_device,
                              int dtype);
+/* lbm_diag of one domain of the batch (the same FP64 reductions of Eq. 7 and the
+ * conservation sums, from the same kernels). Allocates O(cells of the largest domain)
+ * of device scratch on first use (kept until destroy). Synchronises. LBM_E_INVAL for a
+ * bad domain index, LBM_E_STATE before an init, LBM_E_NONFINITE (after filling *out)
+ * when a non-finite moment was found; it then latches for lbm_batch_step. */
+lbm_status lbm_batch_diag(lbm_batch* b, int domain, lbm_diag_t* out);
 /* Total cells of all domains; time step of one domain. */
 lbm_status lbm_batch_info(const lbm_batch* b, long long* total_cells, int domain, double* dt);
 /* Times items per warp (1, 2, 4, 8, 16, 32 tiles of 32 cells) x block sizes x register

@@ -168,6 +168,9 @@ struct lbm_batch {
   unsigned* flag = nullptr;
   float* ghost = nullptr;  // unused by periodic domains; a valid pointer for the plain kernel
   float* trig = nullptr;   // TGV table of the domain being initialised (largest domain's size)
+  float* dufield = nullptr;  // diagnostics scratch, sized for the largest domain (first use)
+  double* dpartials = nullptr;
+  double* dout = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g_pair = nullptr;
@@ -429,6 +432,9 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->flag) cudaFree(b->flag);
   if (b->ghost) cudaFree(b->ghost);
   if (b->trig) cudaFree(b->trig);
+  if (b->dufield) cudaFree(b->dufield);
+  if (b->dpartials) cudaFree(b->dpartials);
+  if (b->dout) cudaFree(b->dout);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return LBM_OK;
@@ -564,6 +570,59 @@ lbm_status lbm_batch_moments(lbm_batch* b, int domain, int which, void* dst, int
   if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(b->stream);
   if (!dst_on_device) cudaFree(dev);
   if (e != cudaSuccess) return fail(LBM_E_CUDA, "batch moments failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_diag(lbm_batch* b, int domain, lbm_diag_t* out) {
+  Range range_("lbm_batch_diag");
+  if (!b || !out) return fail(LBM_E_INVAL, "NULL argument");
+  LBM_ON_DEVICE(b->device);
+  if (domain < 0 || domain >= b->n) return fail(LBM_E_INVAL, "domain index out of range");
+  if (!b->initialized) return fail(LBM_E_STATE, "lbm_batch_diag before an init");
+  if (!b->dufield) {
+    long long most = 0;
+    for (int d = 0; d < b->n; ++d) most = std::max(most, b->P[d].ncell);
+    if (cudaMalloc(&b->dufield, sizeof(float) * 4 * (size_t)most) != cudaSuccess ||
+        cudaMalloc(&b->dpartials, sizeof(double) * (size_t)kDiagBlocks * (kDiagA + 2)) != cudaSuccess ||
+        cudaMalloc(&b->dout, sizeof(double) * 16) != cudaSuccess) {
+      cudaGetLastError();
+      if (b->dufield) cudaFree(b->dufield);
+      if (b->dpartials) cudaFree(b->dpartials);
+      if (b->dout) cudaFree(b->dout);
+      b->dufield = nullptr;
+      b->dpartials = b->dout = nullptr;
+      return fail(LBM_E_NOMEM, "diagnostic scratch allocation failed");
+    }
+  }
+  const DomainConst& P = b->P[domain];
+  double r[16] = {0};
+  unsigned flag = 0;
+  LBM_CUDA(launch_diag(P, b->store, (int)(b->step & 1), domain_pop(b, domain), b->ghost, b->dufield,
+                       b->dpartials, b->dout, b->stream));
+  LBM_CUDA(cudaMemcpyAsync(r, b->dout, sizeof(double) * (kDiagA + 2), cudaMemcpyDeviceToHost,
+                           b->stream));
+  LBM_CUDA(cudaMemcpyAsync(&flag, b->flag, sizeof(flag), cudaMemcpyDeviceToHost, b->stream));
+  LBM_CUDA(cudaStreamSynchronize(b->stream));
+  const double n = (double)P.ncell;
+  out->step = (double)b->step;
+  out->time = (double)b->step * b->dt[domain];
+  out->sum_rho = r[0];
+  out->sum_mx = r[1];
+  out->sum_my = r[2];
+  out->sum_mz = r[3];
+  out->sum_E = r[4];
+  out->ek_mean = r[5] / n;
+  out->nonfinite = r[6];
+  out->max_mach = r[9];
+  out->max_cfl = r[10];
+  out->min_rho = r[11];
+  out->min_T = r[12];
+  out->eps_s_raw = r[13] / n;
+  out->eps_d_raw = 4.0 / 3.0 * r[14] / n;
+  if ((flag & 1u) || r[6] > 0) {
+    b->nonfinite = true;
+    return fail(LBM_E_NONFINITE, "non-finite moments detected");
+  }
   return LBM_OK;
 }
 

@@ -113,6 +113,7 @@ _SIGNATURES = {
     "lbm_batch_synchronize": (_IP, [_VP]),
     "lbm_batch_moments": (_IP, [_VP, _IP, _IP, _VP, _IP, _IP]),
     "lbm_batch_info": (_IP, [_VP, ctypes.POINTER(ctypes.c_longlong), _IP, _DP]),
+    "lbm_batch_diag": (_IP, [_VP, _IP, ctypes.POINTER(LbmDiag)]),
     "lbm_batch_autotune": (_IP, [_VP, _IP, ctypes.POINTER(_IP), ctypes.POINTER(_IP),
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_IP)]),
     "lbm_batch_set_prefetch": (_IP, [_VP, _IP]),
@@ -417,6 +418,16 @@ class Batch:
         check(lib().lbm_batch_moments(self._h, d, which, _np_ptr(out), 0,
                                       DT_F64 if out.dtype == np.float64 else DT_F32))
         return out
+
+    def diag(self, d) -> dict:
+        """lbm_diag of domain d (same keys as Domain.diag)."""
+        r = LbmDiag()
+        st = lib().lbm_batch_diag(self._h, int(d), ctypes.byref(r))
+        res = {n: getattr(r, n) for n in DIAG_FIELDS}
+        if st not in (LBM_OK, LBM_E_NONFINITE):
+            check(st)
+        res["status"] = st
+        return res
 
     def total_cells(self) -> int:
         t = ctypes.c_longlong()

@@ -100,6 +100,7 @@ def test_every_entry_point_rejects_a_null_handle(L):
         "lbm_batch_autotune": (V, 1, V, V, V, V), "lbm_batch_set_prefetch": (V, 0),
         "lbm_test_encode": (1, 0, V, V, V, 4, V),
         "lbm_check_count": (V, V), "lbm_batch_check_count": (V, V),
+        "lbm_batch_diag": (V, 0, V),
     }
     for name, args in calls.items():
         fn = getattr(L, name)

@@ -159,3 +159,28 @@ def test_batch_prefetch_distances_agree_bitwise(lbm, store):
         finally:
             B.close()
     assert ei.value.status == lbm.LBM_E_INVAL
+
+
+def test_batch_diag_equals_single_domain_diag(lbm):
+    """lbm_batch_diag of each domain after an odd number of persistent steps equals
+    lbm_diag of the same domain stepped on its own (the steps are bit-identical, and the
+    diagnostics run the same kernels): every field, including the dissipation integrals
+    and the sums, bit for bit."""
+    params, ic = _small_batch()
+    B = lbm.Batch(params)
+    B.init_tgv([c["U0"] for c in ic], [c["M0"] for c in ic], [c["rho0"] for c in ic])
+    B.step(13)
+    for d, (p, c) in enumerate(zip(params, ic)):
+        one = lbm.Domain(p)
+        one.init_tgv(c["U0"], c["M0"], c["rho0"])
+        one.step(13)
+        want = one.diag()
+        one.close()
+        got = B.diag(d)
+        assert got["status"] == lbm.LBM_OK
+        for k in lbm.DIAG_FIELDS:
+            assert got[k] == want[k], (d, k)
+    with pytest.raises(lbm.LbmError) as ei:
+        B.diag(len(params))
+    assert ei.value.status == lbm.LBM_E_INVAL
+    B.close()
