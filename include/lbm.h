@@ -112,6 +112,21 @@ typedef struct {
                             staged kernel forms round to nearest only; a batch takes one
                             mode for all its domains */
   int use_graphs;        /* 1: lbm_step replays captured CUDA graphs of whole step pairs */
+  int streaming;         /* in-place form of the streaming along the lattice links (Sec. 1,
+                            Sec. 2.2), one population buffer either way (no counterpart in
+                            the paper, which leaves the memory layout open):
+                            0: AA pattern (default): even steps read and write the cell's
+                               own slots, odd steps the slots of its six neighbours;
+                            1: esoteric twist: the slots of the -x, -y, -z directions are
+                               stored with the cell one step along +x, +y, +z, so every
+                               step reads and writes the own cell and one slot of each of
+                               the neighbours x + e_x, x + e_y, x + e_z. The stored buffer
+                               is a fixed permutation of the AA buffer and every result
+                               (populations in canonical order, moments, diagnostics,
+                               checkpoints) is the same bit for bit. Single domains with
+                               the plain kernel forms (variants 0 and 1) only: a batch,
+                               the staged variants and lbm_plane_get/set return
+                               LBM_E_INVAL under it. */
   void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
   void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
                             256-byte aligned, borrowed for the handle's lifetime; NULL:
@@ -310,7 +325,8 @@ lbm_status lbm_populations_set(lbm_handle* h, const void* src, int src_on_device
 /* Writes the parameters, step counter, storage reference and scales, ghost
  * layers and the raw population buffer (canonical order) to `path` with a CRC-32;
  * lbm_load restores them into a handle with the same sizes and storage
- * (LBM_E_INVAL otherwise, LBM_E_IO on a bad file). Resuming is bit-identical. */
+ * (LBM_E_INVAL otherwise, LBM_E_IO on a bad file). Resuming is bit-identical, also
+ * from a handle with the other streaming map (the file holds canonical order). */
 lbm_status lbm_save(lbm_handle* h, const char* path);
 lbm_status lbm_load(lbm_handle* h, const char* path);
 
@@ -329,8 +345,8 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
 /* Fixes the step kernel's form (variant 0-4, see lbm_info_t) and, for variants 0 and
  * 1, its block size (32, 64, 96 or 128 threads; ignored by the staged variants)
  * instead of the defaults or the autotuner's choice. The staged variants need a
- * periodic x axis, nx a multiple of 32 (whole 32-cell tiles per row) and rounding to
- * nearest (LBM_E_INVAL otherwise). All forms compute bit-identical populations. A staged step whose wait
+ * periodic x axis, nx a multiple of 32 (whole 32-cell tiles per row), rounding to
+ * nearest and the AA maps (streaming 0) (LBM_E_INVAL otherwise). All forms compute bit-identical populations. A staged step whose wait
  * for a copy runs out (bounded; it does not happen in normal operation) stops,
  * reports LBM_E_TIMEOUT from the next synchronising call and refuses further steps
  * until a re-init. */
@@ -395,7 +411,8 @@ lbm_status lbm_test_encode(int store, int stochastic_round, const float* in,
  * and after each odd step, that make a ring of slab handles step exactly like the
  * whole domain; the handles must share Q_ref and the storage scales. Asynchronous on
  * the handle's stream for device buffers, synchronous for host buffers.
- * LBM_E_INVAL for z outside [0, nz), slot outside [0, 7) or a NULL buffer. */
+ * LBM_E_INVAL for z outside [0, nz), slot outside [0, 7), a NULL buffer or a handle
+ * under the esoteric twist (streaming 1). */
 lbm_status lbm_plane_get(lbm_handle* h, int z, int slot, void* dst, int dst_on_device);
 lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int src_on_device);
 

@@ -61,6 +61,7 @@ lbm_status validate(const lbm_params* p) {
   if (p->source_mode < 0 || p->source_mode > 1) return fail(LBM_E_INVAL, "source_mode must be 0 or 1");
   if (p->sensor_mode < 0 || p->sensor_mode > 1) return fail(LBM_E_INVAL, "sensor_mode must be 0 or 1");
   if (p->collide < 0 || p->collide > 1) return fail(LBM_E_INVAL, "collide must be 0 or 1");
+  if (p->streaming < 0 || p->streaming > 1) return fail(LBM_E_INVAL, "streaming must be 0 or 1");
   if (p->pop_buffer && (reinterpret_cast<uintptr_t>(p->pop_buffer) & 255u))
     return fail(LBM_E_INVAL, "pop_buffer must be 256-byte aligned");
   return LBM_OK;
@@ -104,6 +105,7 @@ void fill_const(const lbm_params* p, double dt, double tau_R, double tau_q, Doma
   P->sensor_mode = p->sensor_mode;
   P->collide = p->collide;
   P->sround = p->stochastic_round;
+  P->eso = p->streaming;
   P->dx64 = p->dx;
 }
 
@@ -881,6 +883,8 @@ static lbm_status plane_transfer(lbm_handle* h, int z, int slot, void* buf, int 
   LBM_ON_DEVICE(h->device);
   if (z < 0 || z >= h->prm.nz) return fail(LBM_E_INVAL, "plane z = %d outside [0, %d)", z, h->prm.nz);
   if (slot < 0 || slot >= kQ) return fail(LBM_E_INVAL, "slot %d outside [0, 7)", slot);
+  if (h->P.eso)
+    return fail(LBM_E_INVAL, "slot planes follow the AA maps; not available under the esoteric twist");
   const size_t bytes = elem_size(h->prm.store) * kF * (size_t)h->prm.nx * h->prm.ny;
   void* dev = buf;
   if (!on_device) {
@@ -1026,7 +1030,8 @@ lbm_status lbm_set_kernel_config(lbm_handle* h, int block_x, int variant) {
   if (variant >= kFirstStagedVariant) {
     if (!staged_eligible(h->P))
       return fail(LBM_E_INVAL,
-                  "staged variants need periodic x, nx a multiple of 32 and rounding to nearest");
+                  "staged variants need periodic x, nx a multiple of 32, rounding to nearest "
+                  "and the AA maps");
     int grid = 0;
     LBM_CUDA(staged_prepare(h->P, h->prm.store, variant, &grid));
     h->variant = variant;

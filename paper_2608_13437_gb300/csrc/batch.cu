@@ -331,6 +331,10 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
     }
+    if (params[d].streaming != 0) {
+      delete b;
+      return fail(LBM_E_INVAL, "domain %d: the batched mode takes the AA maps (streaming 0)", d);
+    }
     if (params[d].nx > 65535) {  // tile records hold 16-bit coordinates
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes nx <= 65535", d);

@@ -199,7 +199,8 @@ __device__ __forceinline__ void equilibrium_dev(const DomainConst& P, const Init
 }
 
 // mode 0: per-field max |d| into maxbits (for the FP16 scales); mode 1: write the
-// populations (canonical slots: slot i of a cell holds f_i) and the held-x ghosts, and
+// populations (canonical slots: slot i of a cell holds f_i, under the esoteric twist
+// with slots 2, 4, 6 one cell further along +x, +y, +z) and the held-x ghosts, and
 // set *bad (if given) when a cell's state is not finite. Blocks of whole warps, so a
 // warp covers one 32-cell tile.
 template <typename S>
@@ -238,10 +239,20 @@ __global__ void __launch_bounds__(128) k_init(const DomainConst P, const InitSpe
       if (!isfinite(probe)) atomicOr(bad, 1u);
     }
     if (!LBM_CHECK(P, cell < P.ntile * kTile)) continue;
-    S* base = pop + tile_start(cell);
-    const int lane = (int)(cell & (kTile - 1));
+    if (P.eso) {  // esoteric twist: slots 2, 4, 6 live with the cell one step along +x, +y, +z
+      const CellIndex ci = make_index(P, x, y, z);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) store_dir<S>(P, base, i, lane, dev, i, nullptr);
+      for (int i = 0; i < kQ; ++i) {
+        const long long tc = eso_shifted(i) ? ci.nb[i - 1] : cell;
+        if (!LBM_CHECK(P, tc >= 0 && tc < P.ntile * kTile)) continue;
+        store_dir<S>(P, pop + tile_start(tc), i, (int)(tc & (kTile - 1)), dev, i, nullptr);
+      }
+    } else {
+      S* base = pop + tile_start(cell);
+      const int lane = (int)(cell & (kTile - 1));
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) store_dir<S>(P, base, i, lane, dev, i, nullptr);
+    }
     if (P.bc_x && ghost) {
       const long long plane = (long long)y + (long long)P.ny * z;
       if (x == 0)

@@ -49,6 +49,7 @@ struct DomainConst {
   int sutherland, sensor_mode, collide;
   int sround;         // 16-bit storage rounds stochastically (1) or to nearest (0)
   int pf_tiles;       // L2 prefetch distance of the plain step kernel on whole-tile rows (0: off)
+  int eso;            // storage map: 0 AA pattern, 1 esoteric twist (slots 2, 4, 6 shifted)
   double dx64;        // dx in FP64 (the diagnostics' gradient pass takes 1/dx from it)
   unsigned* check;    // checked builds: count of population addresses found outside the buffer
 };
@@ -272,10 +273,37 @@ __device__ __forceinline__ CellIndex make_index(const DomainConst& P, int x, int
   return c;
 }
 
+// Esoteric twist (P.eso): the AA maps with slot s of logical cell x stored with cell
+// x + e_x, x + e_y, x + e_z for s = 2, 4, 6 (the -x, -y, -z slots; periodic wrap), a
+// fixed permutation of the buffer, so every result is the AA result bit for bit. Under
+// it both parities touch the same cells: a step reads the incoming -x, -y, -z
+// populations from the neighbours x + e_x, x + e_y, x + e_z and the rest from the own
+// cell, and writes the outgoing +x, +y, +z populations into those neighbours and the
+// rest into the own cell; the slots alternate as in the AA maps (even steps read slot
+// i and write slot opp(i), odd steps read opp(i) and write i). Each location is still
+// read and then written by one thread, so the update stays in place.
+__device__ __forceinline__ bool eso_shifted(int i) { return i == 2 || i == 4 || i == 6; }
+
+// Cell holding the incoming population of direction i at `parity` (its slot is i on
+// even steps, opp(i) on odd ones).
+__device__ __forceinline__ long long src_cell(const DomainConst& P, const CellIndex& c, int parity,
+                                              int i) {
+  if (P.eso) return eso_shifted(i) ? c.nb[i - 1] : c.own;
+  return parity ? c.nb[opp(i)] : c.own;
+}
+
+// Cell receiving the outgoing population of direction i at `parity` (slot opp(i) on
+// even steps, i on odd ones).
+__device__ __forceinline__ long long dst_cell(const DomainConst& P, const CellIndex& c, int parity,
+                                              int i) {
+  if (P.eso) return (i == 1 || i == 3 || i == 5) ? c.nb[i] : c.own;
+  return parity ? c.nb[i] : c.own;
+}
+
 // Cell and slot from which direction i of this cell is read at `parity`.
 __device__ __forceinline__ long long read_pos(const DomainConst& P, const CellIndex& c, int parity,
                                               int k, int i) {
-  long long cell = parity ? c.nb[opp(i)] : c.own;
+  long long cell = src_cell(P, c, parity, i);
   if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) cell = 0;
   const int slot = parity ? opp(i) : i;
   return pop_index(cell, k, slot);
@@ -296,7 +324,8 @@ __device__ __forceinline__ float ghost_value(const DomainConst& P, const float* 
 }
 
 // Loads the 98 decoded deviations of this cell for a step of the given parity:
-// per direction i the source cell and slot of the AA map, then 4 + 4 + 4 + 2 fields.
+// per direction i the source cell and slot of the AA map (or the esoteric twist), then
+// 4 + 4 + 4 + 2 fields.
 template <int PARITY, bool HELD, typename S>
 __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restrict__ pop,
                                           const float* __restrict__ ghost, const CellIndex& c,
@@ -305,7 +334,7 @@ __device__ __forceinline__ void load_cell(const DomainConst& P, const S* __restr
   using V2 = typename Codec<S>::V2;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const long long cell = PARITY ? c.nb[opp(i)] : c.own;
+    const long long cell = src_cell(P, c, PARITY, i);
     const int slot = PARITY ? opp(i) : i;
     if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) {
 #pragma unroll
@@ -387,7 +416,8 @@ __device__ __forceinline__ void store_dir(const DomainConst& P, S* base, int slo
 }
 
 // Stores the 98 post-collision deviations: direction i goes to the slot and cell of
-// the AA map (own cell, slot opp(i) on even steps; cell x + e_i, slot i on odd steps).
+// the AA map (own cell, slot opp(i) on even steps; cell x + e_i, slot i on odd steps),
+// or of the esoteric twist.
 // SR: stochastic rounding of 16-bit storage (a separate instantiation, so the
 // round-to-nearest kernels carry none of its code).
 template <int PARITY, typename S, bool SR = false>
@@ -397,7 +427,7 @@ __device__ __forceinline__ void store_cell(const DomainConst& P, S* __restrict__
   if constexpr (SR) dz = Dither(c.own, d[0][0], d[4][0]);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const long long cell = PARITY ? c.nb[i] : c.own;
+    const long long cell = dst_cell(P, c, PARITY, i);
     const int slot = PARITY ? i : opp(i);
     if (!LBM_CHECK(P, cell >= 0 && cell < P.ntile * kTile)) continue;
     store_dir<S>(P, pop + tile_start(cell), slot, (int)(cell & (kTile - 1)), d, i,

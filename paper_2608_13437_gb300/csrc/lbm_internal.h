@@ -44,7 +44,8 @@ constexpr int kFirstStagedVariant = 2, kLastStagedVariant = 4;
 constexpr int kDefaultPrefetch16 = 1024;
 constexpr int kMaxPrefetch = 1 << 20;
 inline bool staged_eligible(const DomainConst& P) {
-  return P.bc_x == 0 && P.nx % 32 == 0 && P.sround == 0;  // no stochastic rounding there
+  // no stochastic rounding and no esoteric twist there
+  return P.bc_x == 0 && P.nx % 32 == 0 && P.sround == 0 && P.eso == 0;
 }
 cudaError_t staged_prepare_f32(const DomainConst& P, int variant, int* grid);
 cudaError_t staged_prepare_f16(const DomainConst& P, int variant, int* grid);

@@ -14,8 +14,9 @@ namespace lbm {
 static_assert(kDiagRecFloats == kDiagRecWords, "warp record size");
 
 // ROWS: whole-tile rows (periodic x, nx a multiple of 32) take the plain kernel's
-// warp-uniform tile addressing and its L2 prefetch; every warp is then whole.
-template <int PARITY, typename S, bool HELD, bool SR, bool ROWS>
+// warp-uniform tile addressing and its L2 prefetch; every warp is then whole. ESO: the
+// esoteric twist on whole-tile rows (the other forms take it from P.eso).
+template <int PARITY, typename S, bool HELD, bool SR, bool ROWS, bool ESO = false>
 __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __restrict__ pop,
                                                       const float* __restrict__ ghost,
                                                       unsigned* __restrict__ flag,
@@ -31,8 +32,8 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
     CellDiag cd;
     if constexpr (ROWS) {
       const WarpTiles T = warp_tiles(P, x - lane, blockIdx.y, blockIdx.z);
-      if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S>(P, pop, T.t);
-      load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+      if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S, ESO>(P, pop, T.t);
+      load_cell_rows<PARITY, S, ESO>(P, pop, T, lane, d);
       if (P.collide) {
         const float probe = collide_cell<false, true>(P, d, nullptr, &cd);
         if (!isfinite(probe)) atomicOr(flag, 1u);
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
         SensorOut so;
         collide_cell<true, true>(P, d, &so, &cd);
       }
-      store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
+      store_cell_rows<PARITY, S, SR, ESO>(P, pop, T, lane, d);
     } else {
       const CellIndex c = make_index(P, x, blockIdx.y, blockIdx.z);
       load_cell<PARITY, HELD, S>(P, pop, ghost, c, d);
@@ -75,6 +76,9 @@ void launch_step_diag_forms(const DomainConst& P, int parity, S* p, const float*
   if (P.bc_x) {
     if (parity) k_step_diag<1, S, true, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
     else k_step_diag<0, S, true, SR, false><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+  } else if (P.nx % kTile == 0 && P.eso) {
+    if (parity) k_step_diag<1, S, false, SR, true, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
+    else k_step_diag<0, S, false, SR, true, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
   } else if (P.nx % kTile == 0) {
     if (parity) k_step_diag<1, S, false, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);
     else k_step_diag<0, S, false, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag, ufield, rec);

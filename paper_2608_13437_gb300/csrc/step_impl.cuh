@@ -62,14 +62,27 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
 // a row before, slot 3 of the tile a row after, slot 6 of the tile a plane before and
 // slot 5 of the tile a plane after; prefetching slots 0-4 of tile w (its slots 3 and 4
 // serve the warps a row before and after w) and the two plane slots covers them.
+// Under the esoteric twist every step reads, of tile w, the slots of its own warp and
+// those the warps a tile and a row before it take from w, and the z slot (6 even, 5
+// odd) of the tile a plane after w; the z slot of w itself was read a plane earlier.
 // Only addresses inside the buffer are prefetched (periodic wrap along z); results
 // do not depend on the prefetch.
-template <int PARITY, typename S>
+template <int PARITY, typename S, bool ESO = false>
 __device__ __forceinline__ void prefetch_future(const DomainConst& P, const S* pop, long long t) {
   const long long w = t + P.pf_tiles;
   if (w >= P.ntile) return;
   constexpr unsigned kSlotBytes = kSlotElems * sizeof(S);
-  if (PARITY == 0) {
+  if constexpr (ESO) {
+    const long long tpp = (long long)(P.nx / kTile) * P.ny;
+    const long long zp = w + tpp < P.ntile ? w + tpp : w + tpp - P.ntile;
+    if (PARITY == 0) {
+      l2_prefetch(pop + w * kTileElems, 6 * kSlotBytes);
+    } else {
+      l2_prefetch(pop + w * kTileElems, 5 * kSlotBytes);
+      l2_prefetch(pop + w * kTileElems + 6 * kSlotElems, kSlotBytes);
+    }
+    l2_prefetch(pop + zp * kTileElems + (PARITY ? 5 : 6) * kSlotElems, kSlotBytes);
+  } else if (PARITY == 0) {
     l2_prefetch(pop + w * kTileElems, kQ * kSlotBytes);
   } else {
     const long long tpp = (long long)(P.nx / kTile) * P.ny;
@@ -82,8 +95,9 @@ __device__ __forceinline__ void prefetch_future(const DomainConst& P, const S* p
 }
 
 // load_cell for whole-tile rows: even steps read slot i of the own cell, odd steps
-// slot opp(i) of cell x - e_i.
-template <int PARITY, typename S>
+// slot opp(i) of cell x - e_i; ESO: the esoteric twist, directions -x, -y, -z from the
+// cell x - e_i (= x + e_x, x + e_y, x + e_z) at both parities, the rest from the own cell.
+template <int PARITY, typename S, bool ESO = false>
 __device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __restrict__ pop,
                                                const WarpTiles& T, int lane, float (&d)[kF][kQ]) {
   using V4 = typename Codec<S>::V4;
@@ -92,7 +106,7 @@ __device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __
   for (int i = 0; i < kQ; ++i) {
     long long tile = T.t;
     int ln = lane;
-    if (PARITY && i > 0) link_tile(T, i, -1, lane, tile, ln);
+    if (ESO ? eso_shifted(i) : (PARITY && i > 0)) link_tile(T, i, -1, lane, tile, ln);
     const int slot = PARITY ? opp(i) : i;
     if (!LBM_CHECK(P, tile >= 0 && tile < P.ntile)) {
 #pragma unroll
@@ -114,8 +128,9 @@ __device__ __forceinline__ void load_cell_rows(const DomainConst& P, const S* __
 }
 
 // store_cell for whole-tile rows: even steps write slot opp(i) of the own cell, odd
-// steps slot i of cell x + e_i.
-template <int PARITY, typename S, bool SR = false>
+// steps slot i of cell x + e_i; ESO: directions +x, +y, +z into the cell x + e_i at both
+// parities, the rest into the own cell.
+template <int PARITY, typename S, bool SR = false, bool ESO = false>
 __device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restrict__ pop,
                                                 const WarpTiles& T, int lane,
                                                 const float (&d)[kF][kQ]) {
@@ -125,7 +140,7 @@ __device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restr
   for (int i = 0; i < kQ; ++i) {
     long long tile = T.t;
     int ln = lane;
-    if (PARITY && i > 0) link_tile(T, i, +1, lane, tile, ln);
+    if (ESO ? (i == 1 || i == 3 || i == 5) : (PARITY && i > 0)) link_tile(T, i, +1, lane, tile, ln);
     if (!LBM_CHECK(P, tile >= 0 && tile < P.ntile)) continue;
     store_dir<S>(P, pop + tile * kTileElems, PARITY ? i : opp(i), ln, d, i, SR ? &dz : nullptr);
   }
@@ -135,7 +150,8 @@ __device__ __forceinline__ void store_cell_rows(const DomainConst& P, S* __restr
 // 3 -> at most 170 registers (no spills), 4 -> at most 128 (a few spilled words).
 // ROWS: whole-tile rows (periodic x, nx a multiple of 32), addressed per warp.
 // SR: stochastic rounding of 16-bit storage.
-template <int PARITY, typename S, bool HELD, int MINB, bool ROWS, bool SR = false>
+// ESO: the esoteric twist on whole-tile rows (the other forms take it from P.eso).
+template <int PARITY, typename S, bool HELD, int MINB, bool ROWS, bool SR = false, bool ESO = false>
 __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __restrict__ pop,
                                                     const float* __restrict__ ghost,
                                                     unsigned* __restrict__ flag) {
@@ -145,13 +161,13 @@ __global__ void __launch_bounds__(128, MINB) k_step(const DomainConst P, S* __re
     if (x0 >= P.nx) return;  // whole warps (nx is a multiple of 32)
     const int lane = threadIdx.x & (kTile - 1);
     const WarpTiles T = warp_tiles(P, x0, blockIdx.y, blockIdx.z);
-    if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S>(P, pop, T.t);
-    load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+    if (P.pf_tiles > 0 && lane == 0) prefetch_future<PARITY, S, ESO>(P, pop, T.t);
+    load_cell_rows<PARITY, S, ESO>(P, pop, T, lane, d);
     if (P.collide) {
       const float probe = collide_cell<false>(P, d, nullptr);
       if (!isfinite(probe)) atomicOr(flag, 1u);
     }
-    store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
+    store_cell_rows<PARITY, S, SR, ESO>(P, pop, T, lane, d);
   } else {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= P.nx) return;
@@ -171,6 +187,9 @@ void launch_forms(const DomainConst& P, int parity, S* p, const float* ghost, un
   if (P.bc_x) {
     if (parity) k_step<1, S, true, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
     else k_step<0, S, true, MINB, false, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
+  } else if (P.nx % kTile == 0 && P.eso) {
+    if (parity) k_step<1, S, false, MINB, true, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
+    else k_step<0, S, false, MINB, true, SR, true><<<grid, block, 0, s>>>(P, p, ghost, flag);
   } else if (P.nx % kTile == 0) {
     if (parity) k_step<1, S, false, MINB, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);
     else k_step<0, S, false, MINB, true, SR><<<grid, block, 0, s>>>(P, p, ghost, flag);

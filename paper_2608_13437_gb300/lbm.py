@@ -35,7 +35,7 @@ class LbmParams(ctypes.Structure):
         ("source_mode", ctypes.c_int), ("f_mu", ctypes.c_double), ("C_sigma", ctypes.c_double),
         ("J_min", ctypes.c_double), ("omega_min", ctypes.c_double), ("sensor_mode", ctypes.c_int),
         ("collide", ctypes.c_int), ("store", ctypes.c_int), ("stochastic_round", ctypes.c_int),
-        ("use_graphs", ctypes.c_int),
+        ("use_graphs", ctypes.c_int), ("streaming", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("pop_buffer", ctypes.c_void_p),
     ]
 
@@ -206,6 +206,12 @@ class Domain:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def buffer(self):
+        """The population buffer in its stored layout (torch uint8 tensor on the device),
+        or None when the library allocated it (torch_buffer=False)."""
+        return self._buf
 
     def info(self) -> dict:
         inf = LbmInfo()

@@ -49,7 +49,7 @@ def test_population_bytes_layout(L):
 @pytest.mark.parametrize("field,value,msg", [
     ("nx", 0, "every size"), ("dx", -1.0, "dx"), ("gamma", 1.0, "gamma"),
     ("tau_R", 0.0, "tau_R"), ("omega_min", 2.5, "omega_min"), ("store", 7, "store"),
-    ("J_min", -1.0, "J_min"), ("mu", float("nan"), "mu"),
+    ("J_min", -1.0, "J_min"), ("mu", float("nan"), "mu"), ("streaming", 2, "streaming"),
 ])
 def test_create_rejects_invalid_params_before_any_cuda_call(L, field, value, msg):
     from paper_2608_13437_gb300 import inputs, lbm
@@ -139,6 +139,18 @@ def test_batch_and_params_reject_invalid_stochastic_rounding(L):
     b = ctypes.c_void_p()
     assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
     assert b"one rounding mode" in L.lbm_last_error()
+
+
+def test_batch_rejects_the_esoteric_twist(L):
+    """The batched kernel addresses populations through the AA maps only: a domain
+    with streaming = 1 is refused before any CUDA call."""
+    from paper_2608_13437_gb300 import inputs, lbm
+    arr = (lbm.LbmParams * 2)(lbm.make_params(inputs.tgv_params(8), "f32"),
+                              lbm.make_params(dict(inputs.tgv_params(8), streaming=1), "f32"))
+    b = ctypes.c_void_p()
+    assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
+    assert not b.value
+    assert b"AA maps" in L.lbm_last_error()
 
 
 

@@ -2,7 +2,7 @@
 population tile and ghost address its kernels form is tested against the buffer before
 use, and one outside would be counted (lbm_check_count) instead of faulting. Every entry
 point that moves populations runs on ragged, whole-tile-row, held-x, one-cell,
-stochastically rounded and batched domains; the count must stay zero and the results
+stochastically rounded, esoteric-twist and batched domains; the count must stay zero and the results
 must equal the production build's bit for bit (each build in a child process of its
 own)."""
 import json
@@ -49,8 +49,9 @@ def domain_case(name, p, store, init, steps, sround=0, prefetch=None):
     th, chi, om = d.sensor()
     arrays[name + "_sensor"] = np.stack([th, chi, om])
     arrays[name + "_diag"] = np.array([diag[k] for k in lbm.DIAG_FIELDS])
-    plane = d.plane_get(0, 5, np.empty((14, d.ny, d.nx), dtype=d.plane_dtype(numpy=True)))
-    d.plane_set(0, 5, plane)
+    if not p.get("streaming"):  # slot planes follow the AA maps
+        plane = d.plane_get(0, 5, np.empty((14, d.ny, d.nx), dtype=d.plane_dtype(numpy=True)))
+        d.plane_set(0, 5, plane)
     f = d.populations()
     d.set_populations(f)
     with tempfile.TemporaryDirectory() as tmp:
@@ -72,11 +73,17 @@ q = inputs.tgv_params(16)
 q.update(nx=64, ny=8, nz=4, dx=2 * np.pi / 64)
 domain_case("rows_f16", q, "f16", tgv, 9, prefetch=3)
 domain_case("rows_bf16_sr", q, "bf16", tgv, 5, sround=1)
+domain_case("rows_f16_twist", dict(q, streaming=1), "f16", tgv, 9, prefetch=3)
+domain_case("ragged_f32_twist", dict(p, streaming=1), "f32",
+            lambda d: d.init_fields(s["rho"], s["ux"], s["uy"], s["uz"], s["p"]), 7)
 domain_case("sod_bf16", inputs.sod_params(64), "bf16",
+            lambda d: d.init_riemann(0, 32, inputs.SOD_LEFT, inputs.SOD_RIGHT), 11)
+domain_case("sod_f32_twist", dict(inputs.sod_params(64), streaming=1), "f32",
             lambda d: d.init_riemann(0, 32, inputs.SOD_LEFT, inputs.SOD_RIGHT), 11)
 one = inputs.tgv_params(16)
 one.update(nx=1, ny=1, nz=1)
 domain_case("one_cell", one, "f32", tgv, 3)
+domain_case("one_cell_twist", dict(one, streaming=1), "f32", tgv, 3)
 pl = [inputs.tgv_params(n) for n in (16, 24, 32)]
 b = lbm.Batch(pl)
 b.init_tgv([1.0] * 3, [1.25, 0.9, 0.6], [1.0] * 3)
