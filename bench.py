@@ -38,20 +38,21 @@ KERNEL_SOURCES = ("paper_2608_13437_gb300/csrc/lbm_device.cuh",
                   "paper_2608_13437_gb300/csrc/step_impl.cuh")
 
 
-def bench_config(n, store, world):
+def bench_config(n, store, world, streaming=0):
     """The workload as both arms name it (the reference arm runs the oracle on a window
     of this workload per step; its cpu_baseline says which)."""
     ncell = n ** 3
-    return {"workload": workload_name(n), "n": n, "cells": ncell, "store": store,
+    return {"workload": workload_name(n, streaming), "n": n, "cells": ncell, "store": store,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "l2": "populations (%.1f GB) exceed the 129 MB L2; no flush between steps"
                   % (BYTES_PER_CELL[store] / 2 * ncell / 1e9)}
 
 
-def workload_name(n):
+def workload_name(n, streaming=0):
     return (f"supersonic Taylor-Green vortex {n}^3 periodic [0,2pi)^3, gamma 1.4, Pr 0.71, M0 1.25, "
             "Re 1000, uniform T0, Sutherland, C_sigma 40, J_min 1e-2, omega_min 1.987, "
-            "tau_R = tau_q = 5e-3, CFL 0.1, 14 fields x D3Q7, in-place AA streaming")
+            "tau_R = tau_q = 5e-3, CFL 0.1, 14 fields x D3Q7, in-place "
+            + ("esoteric-twist" if streaming else "AA") + " streaming")
 
 
 def peaks():
@@ -72,7 +73,7 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(store, ncell):
+def traffic_per_launch(store, ncell, streaming=0):
     """DRAM bytes per launch at ncell cells from the committed ncu counters of a smaller
     capture: the reads per cell scale with the cells, and the in-place step writes back
     every line it reads once its state exceeds L2 (at the small capture part of the
@@ -84,7 +85,7 @@ def traffic_per_launch(store, ncell):
             d = json.load(fh)
     except Exception:
         return None
-    ent = d.get(store)
+    ent = d.get(store + ("_esoteric_twist" if streaming else ""))
     if not ent or ent.get("kernel_hash") != kernel_hash():
         return None
     return 2.0 * ent["dram_read_bytes_per_cell"] * ncell
@@ -239,7 +240,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": bench_config(args.n, args.store, world),
+        "config": bench_config(args.n, args.store, world, args.streaming),
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
                          "sample": f"FP64 oracle (two-buffer pull streaming, FP64 arithmetic) on a "
                                    f"{side}^3 window of the {args.n}^3 TGV per step"},
@@ -324,6 +325,44 @@ def diag_costs(torch, dom, ms_step, reps=8):
             "in_step_extra_ms": round(fused - one, 4)}
 
 
+def parity_times(torch, dom, pairs=10):
+    """Mean GPU time of the even and of the odd steps (single launches, a CUDA event
+    between consecutive steps on the handle's stream)."""
+    dom.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * pairs + 1)]
+    first_odd = dom.step_count & 1
+    ev[0].record(dom.stream)
+    for j in range(2 * pairs):
+        dom.step(1)
+        ev[j + 1].record(dom.stream)
+    torch.cuda.synchronize()
+    t = [ev[j].elapsed_time(ev[j + 1]) for j in range(2 * pairs)]
+    a, b = sum(t[0::2]) / pairs, sum(t[1::2]) / pairs
+    even, odd = (b, a) if first_odd else (a, b)
+    return {"even_ms": round(even, 4), "odd_ms": round(odd, 4)}
+
+
+def streaming_leg(torch, lbm, p, store, ncell, steps, warmup, hbm):
+    """The two in-place streaming maps on the same workload and storage: autotuned
+    form, K steps (CUDA events), and the even and odd step times."""
+    out = {"store": store}
+    for name, mode in (("aa", 0), ("esoteric_twist", 1)):
+        d = lbm.Domain(dict(p, streaming=mode), store=store)
+        d.init_tgv(1.0, 1.25, 1.0)
+        tune = d.autotune(pairs_per_trial=3)  # advances the state: re-init below
+        d.init_tgv(1.0, 1.25, 1.0)
+        ms, _ = time_steps(torch, d, steps, max(warmup, 3))
+        par = parity_times(torch, d)
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+        ach = BYTES_PER_CELL[store] * ncell / (ms / steps * 1e-3) / 1e9
+        out[name] = {"value": round(ncell * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                     "ms_per_step": round(ms / steps, 4), "achieved_gbs": round(ach, 1),
+                     "frac": round(ach / hbm, 4), "steps": steps, "tune": tune, **par}
+    return out
+
+
 def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
@@ -374,7 +413,7 @@ def run_gpu(args):
     dev = torch.cuda.current_device()
     n = args.n
     ncell = n ** 3
-    p = inputs.tgv_params(n)
+    p = dict(inputs.tgv_params(n), streaming=args.streaming)
     dom = lbm.Domain(p, store=args.store)
     dom.init_tgv(1.0, 1.25, 1.0)
     tune = dom.autotune(pairs_per_trial=3)   # advances the state: re-init below
@@ -399,7 +438,7 @@ def run_gpu(args):
     hbm, peak_kind = peaks()
     bpc = BYTES_PER_CELL[args.store]
     achieved = bpc * ncell / (ms_total / args.steps * 1e-3) / 1e9
-    traffic = traffic_per_launch(args.store, ncell)
+    traffic = traffic_per_launch(args.store, ncell, args.streaming)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpc * ncell}
@@ -485,6 +524,12 @@ def run_gpu(args):
                 "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4),
                 "steps": k2, "tune": tune2, "stated_err": stated_error(st, sround=sr)}
         variants[args.store] = {"stated_err": stated_error(args.store), "tune": tune}
+        k3 = max(10, min(args.steps, 400))
+        variants["streaming_" + args.store] = streaming_leg(
+            torch, lbm, inputs.tgv_params(n), args.store, ncell, k3, args.warmup, hbm)
+        if args.store != "f16":
+            variants["streaming_f16"] = streaming_leg(
+                torch, lbm, inputs.tgv_params(n), "f16", ncell, k3, args.warmup, hbm)
         variants["diagnostics"] = diag_cost
         variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
         variants["batch64_f16"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup,
@@ -505,7 +550,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": bench_config(n, args.store, world),
+            "config": bench_config(n, args.store, world, args.streaming),
             "roofline": roofline,
             "repeats": {"MLUPS": repeats, "best": max(repeats),
                         "median": sorted(repeats)[1], "steps": [args.steps, rep_steps, rep_steps]},
@@ -528,6 +573,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--store", default="f32", choices=("f32", "f16", "bf16"))
+    ap.add_argument("--streaming", type=int, default=1, choices=(0, 1),
+                    help="in-place streaming map of the single-domain legs: 0 AA pattern, "
+                         "1 esoteric twist (default; both are timed in the streaming legs)")
     ap.add_argument("--impl", default="gpu", choices=("gpu", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage legs")
@@ -558,7 +606,7 @@ def main():
 
         from paper_2608_13437_gb300 import inputs, lbm
         torch.cuda.set_device(0)
-        dom = lbm.Domain(inputs.tgv_params(args.n), store=args.store)
+        dom = lbm.Domain(dict(inputs.tgv_params(args.n), streaming=args.streaming), store=args.store)
         dom.init_tgv(1.0, 1.25, 1.0)
         ms, _ = time_steps(torch, dom, 20, args.warmup)
         out = {"n": args.n, "store": args.store,

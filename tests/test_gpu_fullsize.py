@@ -9,7 +9,7 @@
   * 512^3: the TMA-staged step form against the plain kernel (bit for bit, on the
     device) and the in-step diagnostics against the separate pass;
   * 512^3: the plain step with and without its L2 prefetch (bit for bit, FP32 and
-    FP16);
+    FP16, both streaming maps), and the esoteric twist against the AA maps;
   * dissipation time series per storage type against the oracle (64^3, 400 steps);
   * Sod at 256..2048 cells: shock position, first-order thickness, L1 falling;
   * reduced storage at 128^3 against the FP64 oracle and the FP32 GPU path;
@@ -45,12 +45,13 @@ def rel_l2(a, b):
                                                (40, "f16", 2e-3), (41, "bf16", 2e-2)])
 def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps, store, bound):
     """FP32 within the parity bar; the 16-bit storage modes (the bench's FP16 and BF16
-    legs) within the bounds their 32^3 error tests state."""
+    legs) within the bounds their 32^3 error tests state. The benchmark's configuration:
+    esoteric-twist streaming, autotuned kernel form."""
     import torch
     n, B = 512, 12
     origin = (100, 250, 400)
     p = inputs.tgv_params(n)
-    dom = lbm.Domain(p, store=store)
+    dom = lbm.Domain(dict(p, streaming=1), store=store)
     dom.init_tgv(1.0, 1.25, 1.0)
     dom.autotune(pairs_per_trial=2)  # the benchmark's configuration; re-init after
     dom.init_tgv(1.0, 1.25, 1.0)
@@ -144,13 +145,14 @@ def test_512_staged_form_and_in_step_diagnostics(lbm):
     a.close()
 
 
-@pytest.mark.parametrize("store,pf", [("f32", 512), ("f16", 1024)])
-def test_512_prefetch_form_is_bitwise_equal(lbm, store, pf):
+@pytest.mark.parametrize("store,pf,streaming", [("f32", 512, 0), ("f16", 1024, 0),
+                                                ("f32", 512, 1), ("f16", 1024, 1)])
+def test_512_prefetch_form_is_bitwise_equal(lbm, store, pf, streaming):
     """At 512^3 the plain step with its L2 prefetch (the distance the autotuner picks
     for this size) equals the step without it bit for bit after an odd number of
-    steps, compared on the device."""
+    steps, compared on the device, under either streaming map."""
     import torch
-    p = inputs.tgv_params(512)
+    p = dict(inputs.tgv_params(512), streaming=streaming)
     a = lbm.Domain(p, store=store)
     b = lbm.Domain(p, store=store)
     a.set_kernel_config(64, 0)
@@ -165,6 +167,34 @@ def test_512_prefetch_form_is_bitwise_equal(lbm, store, pf):
     a.close()
     b.close()
     del a, b
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+def test_512_twist_equals_aa(lbm, store):
+    """At 512^3, each map in its autotuned form, the esoteric twist gives the AA maps'
+    zeroth moments (compared on the device) and diagnostics (in the step and separate)
+    bit for bit after an odd number of steps."""
+    import torch
+    p = inputs.tgv_params(512)
+    res = []
+    for mode in (0, 1):
+        d = lbm.Domain(dict(p, streaming=mode), store=store)
+        d.init_tgv(1.0, 1.25, 1.0)
+        d.autotune(pairs_per_trial=1)
+        d.init_tgv(1.0, 1.25, 1.0)
+        d.step(5)
+        in_step = d.step_diag(2)
+        d.synchronize()
+        res.append((d.moments_device(lbm.MOM_Q), in_step, d.diag()))
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+    (qa, ia, sa), (qe, ie, se) = res
+    assert torch.equal(qa, qe)
+    for f in lbm.DIAG_FIELDS:
+        assert ia[f] == ie[f] and sa[f] == se[f], f
+    del res, qa, qe
     torch.cuda.empty_cache()
 
 
