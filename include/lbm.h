@@ -421,13 +421,14 @@ lbm_status lbm_plane_set(lbm_handle* h, int z, int slot, const void* src, int sr
  * F32, F16 or BF16), stored in one buffer on the device current at lbm_batch_create,
  * to which the batch is bound as a handle is (see lbm_create). lbm_batch_step advances all of them by one step per persistent launch
  * (grid = the resident blocks of the GPU; each warp takes items of consecutive
- * 32-cell tiles across all domains, the domain constants staged in shared memory),
+ * 32-cell tiles across all domains and keeps the constants of the domain it works on
+ * in a slot of shared memory of its own),
  * replayed from a CUDA graph; lbm_batch_step_sequential issues one plain launch per
  * domain per step instead. Both give bit-identical populations. Items per warp,
- * block size and register budget come from lbm_batch_autotune. At most a few
- * hundred domains per batch (their constants must fit in shared memory), and each
- * domain's nx at most 65535 (the per-tile records hold 16-bit domain indices and
- * coordinates); LBM_E_INVAL otherwise, before any CUDA call. */
+ * block size and register budget come from lbm_batch_autotune. At most 65535
+ * domains per batch, and each domain's nx at most 65535 (the per-tile records hold
+ * 16-bit domain indices and coordinates); LBM_E_INVAL otherwise, before any CUDA
+ * call. */
 lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out);
 lbm_status lbm_batch_destroy(lbm_batch* b);
 /* Per-domain TGV parameters, arrays of n values (host). */

@@ -1,9 +1,10 @@
 // Batched mode: many independent periodic domains of different sizes and
 // parameters, stored in one buffer, advanced by ONE persistent launch per time
-// step. The grid holds as many blocks as are resident on the GPU. Each block
-// stages every domain's constants in shared memory once; then each warp claims
+// step. The grid holds as many blocks as are resident on the GPU. Each warp claims
 // items from a counter, an item being `tiles_per_item` consecutive 32-cell layout
-// tiles, until none are left. A tile's domain and the (x, y, z) of its first cell
+// tiles, until none are left, and keeps the constants of the domain it is working
+// on in a slot of shared memory of its own, reloaded when its tile belongs to
+// another domain (so the shared memory does not grow with the number of domains). A tile's domain and the (x, y, z) of its first cell
 // come from a per-tile table (one 8-byte record per tile instead of a search and
 // two divisions); no block-wide synchronisation happens after
 // the staging, so warps overlap their loads and arithmetic freely. The per-cell
@@ -29,15 +30,17 @@ namespace batch_kernels {  // named: the host helpers below sit in an anonymous 
 // L2 prefetch for the tile a record names, in the pattern of the single-domain kernel:
 // even steps the tile's 7 slots, odd steps its slots 0-4 and, where a z plane holds
 // whole tiles (every size of the batched workloads), slot 6 of the tile a plane before
-// and slot 5 of the tile a plane after (periodic wrap). Only a hint.
+// and slot 5 of the tile a plane after (periodic wrap). Only a hint; the sizes and the
+// buffer of the record's domain come from the constants in global memory.
 template <int PARITY, typename S>
-__device__ __forceinline__ void prefetch_tile_record(const DomainConst* sP, S* const* sPop, uint2 r) {
+__device__ __forceinline__ void prefetch_tile_record(const DomainConst* __restrict__ consts,
+                                                     void* const* __restrict__ pops, uint2 r) {
   const int lo = (int)(r.x & 0xFFFFu);
-  const DomainConst& P = sP[lo];
+  const DomainConst& P = consts[lo];
   const long long first = (long long)(r.x >> 16) +
                           (long long)P.nx * ((long long)(r.y & 0xFFFFu) + (long long)P.ny * (r.y >> 16));
   const long long w = first / kTile;  // a tile's first cell index is a multiple of 32
-  const S* pop = sPop[lo];
+  const S* pop = static_cast<const S*>(pops[lo]);
   constexpr unsigned kSlotBytes = kSlotElems * sizeof(S);
   if (PARITY == 0) {
     l2_prefetch(pop + w * kTileElems, kQ * kSlotBytes);
@@ -53,26 +56,21 @@ __device__ __forceinline__ void prefetch_tile_record(const DomainConst* sP, S* c
   l2_prefetch(pop + zp * kTileElems + 5 * kSlotElems, kSlotBytes);
 }
 
+constexpr int kBatchMaxWarps = 4;  // blocks of at most 128 threads
+
 template <int PARITY, int MINB, typename S, bool SR>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
                                                           const uint2* __restrict__ tiles,
-                                                          int ndom, int total_tiles,
+                                                          int total_tiles,
                                                           int tiles_per_item, int pf_items,
                                                           unsigned* __restrict__ next_item,
                                                           unsigned* __restrict__ flag) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  DomainConst* sP = reinterpret_cast<DomainConst*>(smem);
-  S** sPop = reinterpret_cast<S**>(sP + ndom);
-  {
-    const int words = ndom * (int)(sizeof(DomainConst) / 4);
-    const int* src = reinterpret_cast<const int*>(consts);
-    int* dst = reinterpret_cast<int*>(sP);
-    for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
-    for (int j = threadIdx.x; j < ndom; j += blockDim.x) sPop[j] = static_cast<S*>(pops[j]);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
+  // the constants and buffer of the domain each warp is on (blocks of at most 4 warps)
+  __shared__ __align__(16) DomainConst sW[kBatchMaxWarps];
+  __shared__ S* sPopW[kBatchMaxWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int cur = -1;  // domain whose constants the warp's slot holds
   const int n_items = (total_tiles + tiles_per_item - 1) / tiles_per_item;
   // Items are claimed in order from one counter (zeroed before the launch), so the
   // tiles in flight stay a compact window of the buffer, as with hardware block
@@ -93,7 +91,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
     if (pf_items > 0) {  // the tiles of the item pf_items ahead, one per lane
       const int fi = item + pf_items, ft = fi * tiles_per_item + lane;
       if (fi < n_items && lane < tiles_per_item && ft < total_tiles)
-        prefetch_tile_record<PARITY, S>(sP, sPop, __ldg(&tiles[ft]));
+        prefetch_tile_record<PARITY, S>(consts, pops, __ldg(&tiles[ft]));
     }
     const int count = min(tiles_per_item, total_tiles - item * tiles_per_item);
     for (int j = 0; j < count; ++j) {
@@ -103,8 +101,17 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
       const int4 ti = make_int4((int)(r0 & 0xFFFFu), (int)(r0 >> 16), (int)(r1 & 0xFFFFu),
                                 (int)(r1 >> 16));
       const int lo = ti.x;
-      const DomainConst& P = sP[lo];
-      S* pop = sPop[lo];
+      if (lo != cur) {  // warp-uniform: reload the warp's slot
+        __syncwarp();   // every lane is done with the previous domain's constants
+        const int* src = reinterpret_cast<const int*>(consts + lo);
+        int* dst = reinterpret_cast<int*>(&sW[warp]);
+        for (int w = lane; w < (int)(sizeof(DomainConst) / 4); w += 32) dst[w] = __ldg(src + w);
+        if (lane == 0) sPopW[warp] = static_cast<S*>(pops[lo]);
+        __syncwarp();
+        cur = lo;
+      }
+      const DomainConst& P = sW[warp];
+      S* pop = sPopW[warp];
       float d[kF][kQ];
       if ((P.nx & (kTile - 1)) == 0) {
         // whole-tile rows: the tile and its neighbour tiles are warp-uniform
@@ -164,7 +171,6 @@ struct lbm_batch {
   int block = 64;
   int variant = 0;             // register budget: 0 -> 3, 1 -> 4 blocks of 128 per SM
   int grid = 0;
-  size_t smem = 0;
   unsigned* flag = nullptr;
   float* ghost = nullptr;  // unused by periodic domains; a valid pointer for the plain kernel
   float* trig = nullptr;   // TGV table of the domain being initialised (largest domain's size)
@@ -211,16 +217,6 @@ auto with_form(const lbm_batch* b, F&& f) {
   return b->sround ? f(Form<__nv_bfloat16, true>{}) : f(Form<__nv_bfloat16, false>{});
 }
 
-template <typename S, bool SR>
-cudaError_t set_smem(size_t smem) {
-  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<0, 3, S, SR>(), attr, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 3, S, SR>(), attr, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<0, 4, S, SR>(), attr, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_ptr<1, 4, S, SR>(), attr, (int)smem);
-  return e;
-}
-
 // Grid size for the current block size and register budget: every block resident.
 lbm_status size_grid(lbm_batch* b) {
   int per_sm = 0;
@@ -229,14 +225,7 @@ lbm_status size_grid(lbm_batch* b) {
     return b->variant ? kernel_ptr<0, 4, typename F::S, F::SR>()
                       : kernel_ptr<0, 3, typename F::S, F::SR>();
   });
-  if (b->smem > 48 * 1024) {
-    cudaError_t e = with_form(b, [&](auto f) {
-      using F = decltype(f);
-      return set_smem<typename F::S, F::SR>(b->smem);
-    });
-    LBM_CUDA(e);
-  }
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, b->smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, 0);
   if (e != cudaSuccess || per_sm < 1) return fail(LBM_E_CUDA, "batched kernel does not fit on an SM");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -253,8 +242,8 @@ void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
   const dim3 g(b->grid), bl(b->block);
   const int pf_items = b->prefetch_tiles > 0 ? std::max(1, b->prefetch_tiles / b->tiles_per_item) : 0;
 #define LBM_BATCH_LAUNCH(PAR, MB)                                                           \
-  k_batch_step<PAR, MB, S, SR><<<g, bl, b->smem, s>>>(b->d_consts, b->d_pops, b->d_tiles, \
-                                                      b->n, b->total_tiles,                 \
+  k_batch_step<PAR, MB, S, SR><<<g, bl, 0, s>>>(b->d_consts, b->d_pops, b->d_tiles,       \
+                                                b->total_tiles,                             \
                                                       b->tiles_per_item, pf_items, b->d_counter, \
                                                       b->flag)
   if (b->variant) {
@@ -382,7 +371,6 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   std::vector<int> prefix(n + 1, 0);
   for (int d = 0; d < n; ++d) prefix[d + 1] = prefix[d] + (int)b->P[d].ntile;
   b->total_tiles = prefix[n];
-  b->smem = sizeof(DomainConst) * n + sizeof(void*) * n;
   std::vector<uint2> tiles((size_t)b->total_tiles);
   for (int d = 0; d < n; ++d) {
     const DomainConst& P = b->P[d];
@@ -393,7 +381,6 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       tiles[(size_t)prefix[d] + j] = make_uint2((unsigned)d | (x0 << 16), y0 | (z0 << 16));
     }
   }
-  if (b->smem > 200 * 1024) return cleanup(fail(LBM_E_INVAL, "too many domains for one batch (%d)", n));
   size_t max_table = 0;
   for (int d = 0; d < n; ++d)
     max_table = std::max(max_table, tgv_table_floats(b->P[d].nx, b->P[d].ny, b->P[d].nz));

@@ -52,6 +52,40 @@ def test_persistent_batch_equals_sequential_launches(lbm):
     b.close()
 
 
+def test_thousands_of_domains_in_one_batch(lbm):
+    """A warp keeps only the constants of the domain it is on, so a batch is not
+    limited by shared memory: 3000 small domains of eight shapes (whole-tile rows,
+    ragged rows, rows shorter than a tile; M0 and Re varying) step bit-identically
+    to per-domain launches, the domain constants being reloaded as warps move on."""
+    shapes = [(8, 8, 8), (32, 2, 3), (5, 3, 2), (40, 3, 1), (64, 1, 2), (16, 4, 4), (7, 7, 7),
+              (33, 2, 2)]
+    params, ic = [], []
+    for j in range(3000):
+        nx, ny, nz = shapes[j % len(shapes)]
+        M0, Re = 0.3 + 0.9 * ((j * 37) % 101) / 100, 100.0 + 15.0 * (j % 97)
+        p = inputs.tgv_params(16, M0=M0, Re=Re)
+        p.update(nx=nx, ny=ny, nz=nz, dx=2 * np.pi / nx)
+        params.append(p)
+        ic.append(inputs.tgv_init(M0=M0))
+    a = lbm.Batch(params)
+    b = lbm.Batch(params)
+    for B in (a, b):
+        B.init_tgv([c["U0"] for c in ic], [c["M0"] for c in ic], [c["rho0"] for c in ic])
+    a.autotune(2)
+    for B in (a, b):
+        B.init_tgv([c["U0"] for c in ic], [c["M0"] for c in ic], [c["rho0"] for c in ic])
+    a.step(7)
+    b.step_sequential(7)
+    a.synchronize()
+    b.synchronize()
+    for d in list(range(0, 3000, 173)) + [2999]:
+        qa, qb = a.moments(d), b.moments(d)
+        assert np.isfinite(qa).all()
+        assert np.array_equal(qa, qb), d
+    a.close()
+    b.close()
+
+
 def test_batch_domain_matches_oracle(lbm, oracle_mod):
     params, ic = _small_batch()
     B = lbm.Batch(params)
