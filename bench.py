@@ -363,6 +363,37 @@ def streaming_leg(torch, lbm, p, store, ncell, steps, warmup, hbm):
     return out
 
 
+def batch_size_sweep(torch, lbm, inputs, steps, warmup, store, cells=40e6, max_domains=700):
+    """Uniform batches of one size each (32^3 ... 128^3 TGV domains, about `cells` cells
+    per batch, at most `max_domains` domains): autotuned persistent launches, K steps
+    timed with CUDA events."""
+    out = []
+    for n in (32, 48, 64, 96, 128):
+        count = min(max_domains, max(1, int(cells // n ** 3)))
+        B = lbm.Batch([inputs.tgv_params(n) for _ in range(count)], store=store)
+        ic = [[1.0] * count, [1.25] * count, [1.0] * count]
+        B.init_tgv(*ic)
+        tune = B.autotune(4)
+        B.init_tgv(*ic)
+        B.step(warmup)
+        B.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(B.stream)
+        B.step(steps)
+        b.record(B.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        total = count * n ** 3
+        out.append({"n": n, "domains": count, "cells": total, "ms_per_step": round(ms, 4),
+                    "value": round(total / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                    "achieved_gbs": round(BYTES_PER_CELL[store] * total / (ms * 1e-3) / 1e9, 1),
+                    "tune": tune})
+        B.close()
+        torch.cuda.empty_cache()
+    return {"store": store, "batches": out}
+
+
 def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
@@ -585,6 +616,9 @@ def main():
     ap.add_argument("--only-diag", action="store_true",
                     help="run only the diagnostics-cost leg (separate pass and in-step) on the "
                          "--n^3 TGV with storage --store")
+    ap.add_argument("--only-batch-sizes", action="store_true",
+                    help="run only uniform batches of 32^3 ... 128^3 domains (about 40 M cells "
+                         "each, storage from --store)")
     ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -599,7 +633,8 @@ def main():
     build.build()
     world, rank, _ = dist_setup()
     args.cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and not args.only_batch and not args.only_diag:
+    if (rank == 0 and world == 1 and not args.no_cpu and not args.only_batch and not args.only_diag
+            and not args.only_batch_sizes):
         args.cpu = cpu_baseline_subprocess(args.n)
     if args.only_diag:
         import torch
@@ -613,6 +648,14 @@ def main():
                "diagnostics": diag_costs(torch, dom, ms / 20)}
         dom.close()
         print(json.dumps(out), flush=True)
+        return
+    if args.only_batch_sizes:
+        import torch
+
+        from paper_2608_13437_gb300 import inputs, lbm
+        torch.cuda.set_device(0)
+        print(json.dumps(batch_size_sweep(torch, lbm, inputs, min(args.steps, 100), args.warmup,
+                                          args.store)), flush=True)
         return
     if args.only_batch:
         import torch
