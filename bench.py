@@ -304,8 +304,12 @@ def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
 
 
 def diag_costs(torch, dom, ms_step, reps=8):
-    """GPU time of one separate FP64 diagnostic pass (lbm_diag) and of one step that
-    computes the diagnostics itself (lbm_step_diag with n = 1), against a plain step."""
+    """GPU time of one separate FP64 diagnostic pass (lbm_diag) and of a step that
+    computes the diagnostics itself, against plain steps. lbm_step_diag blocks the
+    caller until the diagnostics are on the host: with n = 2 the second step is queued
+    behind them and keeps the GPU busy meanwhile (in_step_extra_ms, the GPU cost of the
+    diagnostics); with n = 1 the GPU also idles while the host wakes up and issues the
+    next call (in_step_extra_with_host_wait_ms)."""
     def timed(fn):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -320,9 +324,13 @@ def diag_costs(torch, dom, ms_step, reps=8):
     sep = timed(dom.diag)
     fused = timed(lambda: dom.step_diag(1))
     one = timed(lambda: dom.step(1))  # single plain steps, launched the same way
+    fused2 = timed(lambda: dom.step_diag(2))
+    two = timed(lambda: dom.step(2))
     return {"plain_step_ms": round(ms_step, 4), "single_plain_step_ms": round(one, 4),
             "separate_diag_ms": round(sep, 4), "step_with_diag_ms": round(fused, 4),
-            "in_step_extra_ms": round(fused - one, 4)}
+            "two_steps_ms": round(two, 4), "two_steps_first_with_diag_ms": round(fused2, 4),
+            "in_step_extra_ms": round(fused2 - two, 4),
+            "in_step_extra_with_host_wait_ms": round(fused - one, 4)}
 
 
 def parity_times(torch, dom, pairs=10):

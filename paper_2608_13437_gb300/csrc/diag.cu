@@ -21,9 +21,7 @@ constexpr int kBlock = 256;
 // Reduces one DiagAcc per thread over the block into the FP64 record rec[0..kDiagA).
 __device__ void block_reduce_acc(DiagAcc a, double* __restrict__ rec) {
   __shared__ float sh[kBlock / 32][kDiagRecWords];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  diag_warp_reduce(a);
-  if (lane == 0) diag_store_words(a, sh[warp]);
+  diag_warp_reduce_store(a, sh[threadIdx.x >> 5]);
   __syncthreads();
   if (threadIdx.x == 0) {
     DiagAcc r;
@@ -87,8 +85,9 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 // Pass B: central differences of u (FP32, from the FP32 field), weighted by mu_local;
 // per-cell products in FP32, float-float sums. Work items are columns of 32 x 16 cells
 // (x by y) over kZChunk planes; a grid of resident blocks takes them in a fixed order
-// (block b: items b, b + grid, ...), so sums are reproducible. A block of 256 threads
-// marches up its column; a thread owns 2 consecutive cells of one row. u of the column
+// (block b: items b, b + grid, ...), so sums are reproducible. A block of 128 threads
+// marches up its column; a thread owns 4 consecutive cells of one row (128-bit shared
+// loads). u of the column
 // with a one-cell halo in x and y (wrapped periodically), and mu_local of the column,
 // pass through a ring of kRingB planes in shared memory, filled by asynchronous copies
 // (cp.async) two planes ahead of the plane being differenced, so the DRAM reads of the
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_diag_records(const float* __restrict
 // factor 2); the products of two planes are summed in FP32 before each float-float
 // addition. Every value of the field is read from DRAM about once (the halo comes
 // from L2: neighbouring columns are processed at about the same z).
-constexpr int kCells = 2;  // consecutive cells of a row per thread
+constexpr int kCells = 4;  // consecutive cells of a row per thread
 constexpr int kTileX = 32, kTileY = 16, kZChunk = 32, kRingB = 4;
 constexpr int kThreadsX = kTileX / kCells, kBlockB = kThreadsX * kTileY;
 constexpr int kRowF = kTileX + 8;           // 3 pad, x - 1 halo, 32 cells, x + 32 halo, 3 pad
@@ -413,7 +412,8 @@ int launch_b(const DomainConst& P, const float* ufield, double* pb, cudaStream_t
 // pass A or R, nblocks_b <= nblocks of pass B; one block of kBlock threads): thread t
 // folds blocks t, t + kBlock, ... of every quantity, then a
 // shared-memory tree combines the threads in a fixed pattern. The reference density
-// and energy are added back once per cell at the end.
+// and energy are added back once per cell at the end, the maximum Mach number is the
+// root of the maximum of Mach^2 and the maximum CFL number the maximum speed / c.
 __global__ void __launch_bounds__(kBlock) k_diag_final(const DomainConst P,
                                                        const double* __restrict__ pa,
                                                        const double* __restrict__ pb, int nblocks,
@@ -453,6 +453,8 @@ __global__ void __launch_bounds__(kBlock) k_diag_final(const DomainConst P,
     double v = sh[t][0];
     if (t == 0) v += (double)P.rho_ref * (double)P.ncell;
     if (t == 4) v += (double)P.E_ref * (double)P.ncell;
+    if (t == 9) v = sqrt(v);
+    if (t == 10) v = v / (double)P.c;
     out[t] = v;
   }
 }

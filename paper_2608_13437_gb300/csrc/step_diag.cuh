@@ -62,11 +62,8 @@ __global__ void __launch_bounds__(128, 3) k_step_diag(const DomainConst P, S* __
     ufield[2 * n + cell] = cd.u[2];
     ufield[3 * n + cell] = cd.mu_T;
   }
-  diag_warp_reduce(acc);
-  if (lane == 0) {
-    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    diag_store_words(acc, rec + (blk * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDiagRecWords);
-  }
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  diag_warp_reduce_store(acc, rec + (blk * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDiagRecWords);
 }
 
 template <typename S, bool SR>
