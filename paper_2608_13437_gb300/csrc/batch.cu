@@ -4,11 +4,11 @@
 // items from a counter, an item being `tiles_per_item` consecutive 32-cell layout
 // tiles, until none are left, and keeps the constants of the domain it is working
 // on in a slot of shared memory of its own, reloaded when its tile belongs to
-// another domain (so the shared memory does not grow with the number of domains). A tile's domain and the (x, y, z) of its first cell
-// come from a per-tile table (one 8-byte record per tile instead of a search and
-// two divisions); no block-wide synchronisation happens after
-// the staging, so warps overlap their loads and arithmetic freely. The per-cell
-// update is the single-domain one; domains whose rows are whole tiles use its
+// another domain (so the shared memory does not grow with the number of domains).
+// A tile's domain and the (x, y, z) of its first cell come from a per-tile table
+// (one 8-byte record per tile instead of a search and two divisions); no block-wide
+// synchronisation happens, so warps overlap their loads and arithmetic freely. The
+// per-cell update is the single-domain one; domains whose rows are whole tiles use its
 // warp-uniform tile addressing. Items per warp, block size and register budget
 // come from the autotuner; the step pair is replayed from a CUDA graph. 16-bit
 // batches may round stochastically (one mode for the whole batch; a separate
