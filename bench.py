@@ -195,11 +195,11 @@ CPU_WINDOW = 160  # side of the oracle's window of the TGV, as in the reference 
 
 
 def cpu_baseline(n_global, budget_s=15.0):
-    """Bounded sample: calibrate on 32^3, then time a 160^3 window (the reference arm's
-    largest window) for as many steps as fit in about budget_s seconds."""
-    rate, _, thr = time_oracle(n_global, 32, 2, 0)
+    """Bounded sample: time one step of a 160^3 window (the reference arm's largest
+    window), then that window for as many steps as fit in about budget_s seconds."""
     side = CPU_WINDOW
-    steps = max(1, min(50, int(budget_s * rate * 1e6 / side ** 3)))
+    _, one_step, thr = time_oracle(n_global, side, 1, 0)
+    steps = max(1, min(50, int(budget_s / max(one_step, 1e-3))))
     mlups, secs, thr = time_oracle(n_global, side, steps, 1)
     # the same code on one core, on a 64^3 window for about 3 s
     from oracle.oracle import set_threads
