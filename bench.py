@@ -402,19 +402,21 @@ def batch_size_sweep(torch, lbm, inputs, steps, warmup, store, cells=40e6, max_d
     return {"store": store, "batches": out}
 
 
-def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0):
+def batch_leg(torch, lbm, inputs, steps, warmup, n_domains=64, store="f32", sround=0,
+              streaming=0):
     """Independent TGV domains (sizes, M0, Re from SplitMix64(0); 64 by default): one
     persistent launch per step (CUDA graph, autotuned tiles) against one plain launch
     per domain per step."""
     doms = inputs.batch_domains()[:n_domains]
     pl = inputs.batch_params(doms)
-    B = lbm.Batch([dict(q, stochastic_round=sround) for q, _ in pl], store=store)
+    B = lbm.Batch([dict(q, stochastic_round=sround, streaming=streaming) for q, _ in pl],
+                  store=store)
     ic = [[c["U0"] for _, c in pl], [c["M0"] for _, c in pl], [c["rho0"] for _, c in pl]]
     B.init_tgv(*ic)
     tune = B.autotune(4)
     cells = B.total_cells()
     out = {"domains": len(doms), "cells": cells, "store": store, "stochastic_round": sround,
-           "tune": tune}
+           "streaming": "esoteric twist" if streaming else "AA", "tune": tune}
     for name, fn in (("persistent", B.step), ("sequential", B.step_sequential)):
         B.init_tgv(*ic)
         fn(warmup)
@@ -570,11 +572,13 @@ def run_gpu(args):
             variants["streaming_f16"] = streaming_leg(
                 torch, lbm, inputs.tgv_params(n), "f16", ncell, k3, args.warmup, hbm)
         variants["diagnostics"] = diag_cost
-        variants["batch64"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup)
-        variants["batch64_f16"] = batch_leg(torch, lbm, inputs, min(args.steps, 200), args.warmup,
-                                            store="f16")
+        kb = min(args.steps, 200)
+        variants["batch64"] = batch_leg(torch, lbm, inputs, kb, args.warmup,
+                                        streaming=args.streaming)
+        variants["batch64_f16"] = batch_leg(torch, lbm, inputs, kb, args.warmup, store="f16",
+                                            streaming=args.streaming)
         variants["batch64_f16_stochastic_rounding"] = batch_leg(
-            torch, lbm, inputs, min(args.steps, 200), args.warmup, store="f16", sround=1)
+            torch, lbm, inputs, kb, args.warmup, store="f16", sround=1, streaming=args.streaming)
 
     cpu = args.cpu
     if cpu is not None and not args.no_variants:
@@ -671,7 +675,7 @@ def main():
         from paper_2608_13437_gb300 import inputs, lbm
         torch.cuda.set_device(0)
         print(json.dumps(batch_leg(torch, lbm, inputs, args.steps, args.warmup, args.only_batch,
-                                   store=args.store)), flush=True)
+                                   store=args.store, streaming=args.streaming)), flush=True)
         return
     run_gpu(args)
 

@@ -123,10 +123,9 @@ typedef struct {
                                the neighbours x + e_x, x + e_y, x + e_z. The stored buffer
                                is a fixed permutation of the AA buffer and every result
                                (populations in canonical order, moments, diagnostics,
-                               checkpoints) is the same bit for bit. Single domains with
-                               the plain kernel forms (variants 0 and 1) only: a batch,
-                               the staged variants and lbm_plane_get/set return
-                               LBM_E_INVAL under it. */
+                               checkpoints) is the same bit for bit. The staged variants
+                               and lbm_plane_get/set return LBM_E_INVAL under it; a batch
+                               takes one map for all its domains. */
   void* cuda_stream;     /* cudaStream_t to issue work on (borrowed), or NULL */
   void* pop_buffer;      /* optional device buffer of lbm_population_bytes() bytes,
                             256-byte aligned, borrowed for the handle's lifetime; NULL:

@@ -32,7 +32,7 @@ namespace batch_kernels {  // named: the host helpers below sit in an anonymous 
 // whole tiles (every size of the batched workloads), slot 6 of the tile a plane before
 // and slot 5 of the tile a plane after (periodic wrap). Only a hint; the sizes and the
 // buffer of the record's domain come from the constants in global memory.
-template <int PARITY, typename S>
+template <int PARITY, typename S, bool ESO>
 __device__ __forceinline__ void prefetch_tile_record(const DomainConst* __restrict__ consts,
                                                      void* const* __restrict__ pops, uint2 r) {
   const int lo = (int)(r.x & 0xFFFFu);
@@ -42,6 +42,16 @@ __device__ __forceinline__ void prefetch_tile_record(const DomainConst* __restri
   const long long w = first / kTile;  // a tile's first cell index is a multiple of 32
   const S* pop = static_cast<const S*>(pops[lo]);
   constexpr unsigned kSlotBytes = kSlotElems * sizeof(S);
+  if constexpr (ESO) {  // the single-domain kernel's pattern under the esoteric twist
+    l2_prefetch(pop + w * kTileElems, (PARITY ? 5 : 6) * kSlotBytes);
+    if (PARITY) l2_prefetch(pop + w * kTileElems + 6 * kSlotElems, kSlotBytes);
+    const long long plane = (long long)P.nx * P.ny;
+    if (plane % kTile) return;
+    const long long tpp = plane / kTile;
+    const long long zp = w + tpp < P.ntile ? w + tpp : w + tpp - P.ntile;
+    l2_prefetch(pop + zp * kTileElems + (PARITY ? 5 : 6) * kSlotElems, kSlotBytes);
+    return;
+  }
   if (PARITY == 0) {
     l2_prefetch(pop + w * kTileElems, kQ * kSlotBytes);
     return;
@@ -58,7 +68,9 @@ __device__ __forceinline__ void prefetch_tile_record(const DomainConst* __restri
 
 constexpr int kBatchMaxWarps = 4;  // blocks of at most 128 threads
 
-template <int PARITY, int MINB, typename S, bool SR>
+// ESO: every domain under the esoteric twist (whole-tile rows take it as a compile-time
+// form; the other domains from their constants).
+template <int PARITY, int MINB, typename S, bool SR, bool ESO>
 __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __restrict__ consts,
                                                           void* const* __restrict__ pops,
                                                           const uint2* __restrict__ tiles,
@@ -91,7 +103,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
     if (pf_items > 0) {  // the tiles of the item pf_items ahead, one per lane
       const int fi = item + pf_items, ft = fi * tiles_per_item + lane;
       if (fi < n_items && lane < tiles_per_item && ft < total_tiles)
-        prefetch_tile_record<PARITY, S>(consts, pops, __ldg(&tiles[ft]));
+        prefetch_tile_record<PARITY, S, ESO>(consts, pops, __ldg(&tiles[ft]));
     }
     const int count = min(tiles_per_item, total_tiles - item * tiles_per_item);
     for (int j = 0; j < count; ++j) {
@@ -116,10 +128,10 @@ __global__ void __launch_bounds__(128, MINB) k_batch_step(const DomainConst* __r
       if ((P.nx & (kTile - 1)) == 0) {
         // whole-tile rows: the tile and its neighbour tiles are warp-uniform
         const WarpTiles T = warp_tiles(P, ti.y, ti.z, ti.w);
-        load_cell_rows<PARITY, S>(P, pop, T, lane, d);
+        load_cell_rows<PARITY, S, ESO>(P, pop, T, lane, d);
         const float probe = collide_cell<false>(P, d, nullptr);
         if (!isfinite(probe)) atomicOr(flag, 1u);
-        store_cell_rows<PARITY, S, SR>(P, pop, T, lane, d);
+        store_cell_rows<PARITY, S, SR, ESO>(P, pop, T, lane, d);
       } else {
         const int first = ti.y + P.nx * (ti.z + P.ny * ti.w);
         if (first + lane < P.ncell) {
@@ -160,6 +172,7 @@ struct lbm_batch {
   void* pool = nullptr;
   int store = LBM_STORE_F32;
   bool sround = false;         // 16-bit storage rounded stochastically (all domains)
+  bool eso = false;            // esoteric-twist streaming (all domains)
   DomainConst* d_consts = nullptr;
   void** d_pops = nullptr;
   unsigned* d_maxbits = nullptr;  // per-field maxima for the FP16 scales at init
@@ -197,24 +210,30 @@ namespace {
 
 void* domain_pop(lbm_batch* b, int d) { return static_cast<char*>(b->pool) + b->offset[d]; }
 
-template <int P, int M, typename S, bool SR>
+template <int P, int M, typename S, bool SR, bool ESO>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(k_batch_step<P, M, S, SR>);
+  return reinterpret_cast<void*>(k_batch_step<P, M, S, SR, ESO>);
 }
 
-template <typename S_, bool SR_>
+template <typename S_, bool SR_, bool ESO_>
 struct Form {
   using S = S_;
   static constexpr bool SR = SR_;
+  static constexpr bool ESO = ESO_;
 };
 
-// Calls f with the Form (storage type, rounding) of the batch's kernels.
+template <bool ESO, typename F>
+auto with_form_map(const lbm_batch* b, F&& f) {
+  if (b->store == LBM_STORE_F32) return f(Form<float, false, ESO>{});
+  if (b->store == LBM_STORE_F16)
+    return b->sround ? f(Form<__half, true, ESO>{}) : f(Form<__half, false, ESO>{});
+  return b->sround ? f(Form<__nv_bfloat16, true, ESO>{}) : f(Form<__nv_bfloat16, false, ESO>{});
+}
+
+// Calls f with the Form (storage type, rounding, streaming map) of the batch's kernels.
 template <typename F>
 auto with_form(const lbm_batch* b, F&& f) {
-  if (b->store == LBM_STORE_F32) return f(Form<float, false>{});
-  if (b->store == LBM_STORE_F16)
-    return b->sround ? f(Form<__half, true>{}) : f(Form<__half, false>{});
-  return b->sround ? f(Form<__nv_bfloat16, true>{}) : f(Form<__nv_bfloat16, false>{});
+  return b->eso ? with_form_map<true>(b, f) : with_form_map<false>(b, f);
 }
 
 // Grid size for the current block size and register budget: every block resident.
@@ -222,8 +241,8 @@ lbm_status size_grid(lbm_batch* b) {
   int per_sm = 0;
   void* fn = with_form(b, [&](auto f) {
     using F = decltype(f);
-    return b->variant ? kernel_ptr<0, 4, typename F::S, F::SR>()
-                      : kernel_ptr<0, 3, typename F::S, F::SR>();
+    return b->variant ? kernel_ptr<0, 4, typename F::S, F::SR, F::ESO>()
+                      : kernel_ptr<0, 3, typename F::S, F::SR, F::ESO>();
   });
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->block, 0);
   if (e != cudaSuccess || per_sm < 1) return fail(LBM_E_CUDA, "batched kernel does not fit on an SM");
@@ -237,15 +256,14 @@ lbm_status size_grid(lbm_batch* b) {
   return LBM_OK;
 }
 
-template <typename S, bool SR>
+template <typename S, bool SR, bool ESO>
 void launch_typed(lbm_batch* b, int parity, cudaStream_t s) {
   const dim3 g(b->grid), bl(b->block);
   const int pf_items = b->prefetch_tiles > 0 ? std::max(1, b->prefetch_tiles / b->tiles_per_item) : 0;
 #define LBM_BATCH_LAUNCH(PAR, MB)                                                           \
-  k_batch_step<PAR, MB, S, SR><<<g, bl, 0, s>>>(b->d_consts, b->d_pops, b->d_tiles,       \
-                                                b->total_tiles,                             \
-                                                      b->tiles_per_item, pf_items, b->d_counter, \
-                                                      b->flag)
+  k_batch_step<PAR, MB, S, SR, ESO><<<g, bl, 0, s>>>(b->d_consts, b->d_pops, b->d_tiles,  \
+                                                     b->total_tiles, b->tiles_per_item,     \
+                                                     pf_items, b->d_counter, b->flag)
   if (b->variant) {
     if (parity) LBM_BATCH_LAUNCH(1, 4);
     else LBM_BATCH_LAUNCH(0, 4);
@@ -262,7 +280,7 @@ cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   with_form(b, [&](auto f) {
     using F = decltype(f);
-    launch_typed<typename F::S, F::SR>(b, parity, s);
+    launch_typed<typename F::S, F::SR, F::ESO>(b, parity, s);
   });
   return cudaGetLastError();
 }
@@ -308,6 +326,7 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
   b->n = n;
   b->store = params[0].store;
   b->sround = params[0].stochastic_round != 0 && params[0].store != LBM_STORE_F32;
+  b->eso = params[0].streaming == 1;
   b->prefetch_tiles = b->store == LBM_STORE_F32 ? 0 : kDefaultPrefetch16;
   size_t bytes = 0;
   for (int d = 0; d < n; ++d) {
@@ -320,9 +339,9 @@ lbm_status lbm_batch_create(int n, const lbm_params* params, lbm_batch** out) {
       delete b;
       return fail(LBM_E_INVAL, "domain %d: the batched mode takes periodic domains of one storage type", d);
     }
-    if (params[d].streaming != 0) {
+    if (params[d].streaming != params[0].streaming) {
       delete b;
-      return fail(LBM_E_INVAL, "domain %d: the batched mode takes the AA maps (streaming 0)", d);
+      return fail(LBM_E_INVAL, "domain %d: the batched mode takes one streaming map (streaming)", d);
     }
     if (params[d].nx > 65535) {  // tile records hold 16-bit coordinates
       delete b;

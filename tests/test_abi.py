@@ -141,17 +141,16 @@ def test_batch_and_params_reject_invalid_stochastic_rounding(L):
     assert b"one rounding mode" in L.lbm_last_error()
 
 
-def test_batch_rejects_the_esoteric_twist(L):
-    """The batched kernel addresses populations through the AA maps only: a domain
-    with streaming = 1 is refused before any CUDA call."""
+def test_batch_rejects_mixed_streaming_maps(L):
+    """A batch takes one streaming map for all its domains (its persistent kernel is
+    compiled per map): mixed maps are refused before any CUDA call."""
     from paper_2608_13437_gb300 import inputs, lbm
     arr = (lbm.LbmParams * 2)(lbm.make_params(inputs.tgv_params(8), "f32"),
                               lbm.make_params(dict(inputs.tgv_params(8), streaming=1), "f32"))
     b = ctypes.c_void_p()
     assert L.lbm_batch_create(2, arr, ctypes.byref(b)) == lbm.LBM_E_INVAL
     assert not b.value
-    assert b"AA maps" in L.lbm_last_error()
-
+    assert b"one streaming map" in L.lbm_last_error()
 
 
 def test_batch_rejects_more_domains_or_wider_rows_than_its_tile_records_hold(L):
