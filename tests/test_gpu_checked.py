@@ -93,6 +93,15 @@ for j in range(3):
     arrays[f"batch_{j}"] = b.moments(j)
 count("batch", lbm.lib().lbm_batch_check_count, b._h)
 b.close()
+b = lbm.Batch([dict(q, streaming=1) for q in pl], store="f16")
+b.init_tgv([1.0] * 3, [1.25, 0.9, 0.6], [1.0] * 3)
+b.set_prefetch(2)
+b.step(5)
+b.step_sequential(2)
+for j in range(3):
+    arrays[f"batch_twist_{j}"] = b.moments(j)
+count("batch_twist", lbm.lib().lbm_batch_check_count, b._h)
+b.close()
 np.savez(sys.argv[1], **arrays)
 print(json.dumps(counts))
 """
