@@ -75,13 +75,14 @@ def test_tgv_512_light_cone_matches_oracle(lbm, oracle_mod, steps, store, bound)
     assert max(errs.values()) < bound, errs
 
 
-def test_largest_fp32_domain_matches_oracle_on_light_cones(lbm, oracle_mod):
+@pytest.mark.parametrize("streaming", [0, 1])
+def test_largest_fp32_domain_matches_oracle_on_light_cones(lbm, oracle_mod, streaming):
     """The largest cube whose FP32 populations (392 B per cell, 216 GiB at 840^3:
     593 M cells, 5.8e10 stored values) and a primitive readback fit on the GPU with a
     margin: after 9 steps, windows in the interior and across the periodic corner
     (the highest cell indices, wrapping to the lowest) match the oracle's light-cone
-    recomputation at the FP32 tolerance. Skipped when the free device memory is
-    short."""
+    recomputation at the FP32 tolerance, under either streaming map. Skipped when the
+    free device memory is short."""
     import torch
     n, B, steps = 840, 10, 9
     torch.cuda.empty_cache()
@@ -90,7 +91,7 @@ def test_largest_fp32_domain_matches_oracle_on_light_cones(lbm, oracle_mod):
     if free < need:
         pytest.skip(f"needs {need / 2**30:.0f} GiB free, {free / 2**30:.0f} GiB available")
     p = inputs.tgv_params(n)
-    dom = lbm.Domain(p)
+    dom = lbm.Domain(dict(p, streaming=streaming))
     dom.init_tgv(1.0, 1.25, 1.0)
     dom.step(steps)
     dom.synchronize()
