@@ -245,9 +245,10 @@ lbm_status lbm_init_state(lbm_handle* h, const void* Q, int src_on_device, int d
 
 /* Advances n >= 0 time steps: per step one fused kernel reads each cell's 98
  * populations (AA pattern: own slots on even steps, the neighbours' slots on odd
- * steps), computes moments, closure, sensor and collision in FP32 and writes the
- * 98 post-collision populations back in place, so that streaming happens through
- * the index maps. Asynchronous on the handle's stream. Returns LBM_E_STATE before
+ * steps; esoteric twist: own slots and one slot of each of the +x, +y, +z
+ * neighbours on every step; lbm_params.streaming), computes moments, closure,
+ * sensor and collision in FP32 and writes the 98 post-collision populations back
+ * in place, so that streaming happens through the index maps. Asynchronous on the handle's stream. Returns LBM_E_STATE before
  * an init, LBM_E_NONFINITE if an earlier synchronising call saw non-finite
  * moments (no work is issued then). */
 lbm_status lbm_step(lbm_handle* h, int n);
@@ -345,7 +346,8 @@ lbm_status lbm_autotune(lbm_handle* h, int pairs_per_trial, lbm_tune_t* out);
  * 1, its block size (32, 64, 96 or 128 threads; ignored by the staged variants)
  * instead of the defaults or the autotuner's choice. The staged variants need a
  * periodic x axis, nx a multiple of 32 (whole 32-cell tiles per row), rounding to
- * nearest and the AA maps (streaming 0) (LBM_E_INVAL otherwise). All forms compute bit-identical populations. A staged step whose wait
+ * nearest and the AA maps (streaming 0) (LBM_E_INVAL otherwise). All forms compute
+ * bit-identical populations. A staged step whose wait
  * for a copy runs out (bounded; it does not happen in normal operation) stops,
  * reports LBM_E_TIMEOUT from the next synchronising call and refuses further steps
  * until a re-init. */
