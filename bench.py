@@ -276,6 +276,29 @@ def stated_error(store, n=32, steps=100, sround=0):
             "case": f"TGV {n}^3, {steps} steps, vs FP64 oracle"}
 
 
+LONG_RUN = (128, 5000, 250)  # TGV size, steps, diagnostic interval of the drift statement
+
+
+def long_run_curves(store, sround=0):
+    """E_k, eps_s, eps_d every LONG_RUN[2] steps over LONG_RUN[1] steps of the TGV at
+    LONG_RUN[0]^3, computed inside the step."""
+    from paper_2608_13437_gb300 import tgv_series
+    n, steps, every = LONG_RUN
+    res = tgv_series.run(n, steps, every, store, overrides={"stochastic_round": sround})
+    return {k: [x[k] for x in res["samples"]] for k in ("E_k", "eps_s", "eps_d")}
+
+
+def long_run_error(curves, ref):
+    """Largest deviation from the FP32 path's curves over the run, divided by the
+    curve's largest value."""
+    n, steps, every = LONG_RUN
+    out = {k: round(max(abs(a - b) for a, b in zip(curves[k], ref[k])) / max(ref[k]), 8)
+           for k in ref}
+    out["case"] = (f"TGV {n}^3, {steps} steps, E_k / eps_s / eps_d every {every} steps "
+                   "vs the FP32 path (largest deviation / largest value)")
+    return out
+
+
 def time_steps(torch, dom, steps, warmup, dist=None, sampler_index=None):
     stream = dom.stream
     dom.step(warmup)
@@ -547,6 +570,7 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants and rank == 0:
+        ref_curves = long_run_curves("f32")
         for st, sr in (("f16", 0), ("bf16", 0), ("f16", 1), ("bf16", 1)):
             if st == args.store:
                 continue
@@ -563,7 +587,8 @@ def run_gpu(args):
             variants[st + ("_stochastic_rounding" if sr else "")] = {
                 "value": round(ncell * k2 / (ms2 * 1e-3) / 1e6, 1), "unit": "MLUPS",
                 "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4),
-                "steps": k2, "tune": tune2, "stated_err": stated_error(st, sround=sr)}
+                "steps": k2, "tune": tune2, "stated_err": stated_error(st, sround=sr),
+                "stated_err_long_run": long_run_error(long_run_curves(st, sr), ref_curves)}
         variants[args.store] = {"stated_err": stated_error(args.store), "tune": tune}
         k3 = max(10, min(args.steps, 400))
         variants["streaming_" + args.store] = streaming_leg(
