@@ -43,14 +43,16 @@ def prim_errors(gpu, ref):
 @pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("shape,steps", [((5, 4, 3), 1), ((5, 4, 3), 2), ((37, 6, 5), 7),
                                          ((1, 1, 1), 3), ((64, 3, 2), 10)])
-def test_streaming_bit_exact(lbm, oracle_mod, store, shape, steps):
-    """Collision off: the AA index maps must realise f_i(x) <- f_i(x - e_i) exactly,
-    for odd and even step counts, ragged sizes and a single cell. The expected
-    values come from the oracle's pull streaming of the same labels."""
+@pytest.mark.parametrize("streaming", [0, 1])
+def test_streaming_bit_exact(lbm, oracle_mod, store, shape, steps, streaming):
+    """Collision off: the in-place index maps (the AA pattern and the esoteric twist)
+    must realise f_i(x) <- f_i(x - e_i) exactly, for odd and even step counts, ragged
+    sizes, whole-tile rows and a single cell. The expected values come from the
+    oracle's pull streaming of the same labels."""
     nx, ny, nz = shape
     p = inputs.tgv_params(8)
     p.update(nx=nx, ny=ny, nz=nz, collide=0)
-    dom = lbm.Domain(p, store=store)
+    dom = lbm.Domain(dict(p, streaming=streaming), store=store)
     if store == "f32":
         lab = inputs.random_labels((NF, NQ, nz, ny, nx), seed=3, dtype=np.float32)
         ref_in = lab.astype(np.float64)
